@@ -1,0 +1,326 @@
+"""Benchmark: FPS of the sort-free renderer at 1600x1063 with 600k Gaussians.
+
+Workload (synthetic stand-in for the paper's Mip-NeRF 360 "unbounded"
+scenes): 600k Gaussians, 80 % in an ellipsoid of radii (4, 2, 4) and 20 % on a
+far shell, FP16 attributes, BF16 enhancement MLP (2 x 64 hidden), 64 camera
+poses on an orbit of radius 8.  One step = one sweep over the 64 poses
+(64 frames through preprocess + MLP + binning + rasterisation).
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on the
+host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FPS @1600x1063/600k Gaussians; served views/s + p50/p99 latency vs plain"
+N_POSES = 64
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3][k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_sample(tile_stride: int = 32, pose: int = 0):
+    """Time the FP64 oracle as it stands (single thread) on one pose of the
+    workload: full preprocessing (600k Gaussians incl. MLP) and binning, and
+    rasterisation of every `tile_stride`-th tile, scaled to the whole frame."""
+    import oracle
+    from paper_2603_11531_gb300 import synth
+    oracle.build()
+    scene, cams = synth.workload_unbounded_600k(n_poses=N_POSES)
+    cam = cams[pose]
+    t0 = time.perf_counter()
+    g = oracle.preprocess(scene.attrs, cam, scene.mlp, use_mlp=True)
+    off, gids = oracle.bin_tiles(g, cam.width, cam.height)
+    t1 = time.perf_counter()
+    tx, ty = oracle.tiles(cam.width, cam.height)
+    T = tx * ty
+    t_r = 0.0
+    for t in range(0, T, tile_stride):
+        s = time.perf_counter()
+        oracle.rasterize(g, off, gids, cam.width, cam.height, tile_range=(t, t + 1))
+        t_r += time.perf_counter() - s
+    n_sampled = len(range(0, T, tile_stride))
+    frame_s = (t1 - t0) + t_r * T / n_sampled
+    return {"value": 1.0 / frame_s, "unit": "FPS", "cores": 1, "kind": "oracle",
+            "sample": (f"pose {pose}: preprocess+MLP+binning of all 600k Gaussians "
+                       f"({t1 - t0:.1f} s) + rasterisation of {n_sampled}/{T} tiles "
+                       f"(every {tile_stride}th, {t_r:.1f} s), scaled to a full frame"),
+            "seconds": (t1 - t0) + t_r}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    steps = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        # each step: a bounded sample of the frame (every 64th tile), scaled
+        r = cpu_baseline_sample(tile_stride=64, pose=i % N_POSES)
+        if i >= args.warmup:
+            steps.append(1.0 / r["value"])
+            cb = r
+    fps = len(steps) / sum(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "FPS",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(steps) / len(steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "unbounded_600k_fp16_mlp_1600x1063_orbit64",
+                       "step": "one frame (bounded tile sample, scaled)"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": fps, "unit": "FPS",
+                             "sample": cb["sample"] if cb else ""},
+            "e2e": {"value": fps, "unit": "FPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import paper_2603_11531_gb300 as m
+    from paper_2603_11531_gb300 import synth
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    scene, cams = synth.workload_unbounded_600k(n_poses=N_POSES)
+    r = m.Renderer(local)
+    h = r.load_scene(scene)
+    opts = m.render_opts(use_mlp=True)
+    H, W = cams[0].height, cams[0].width
+    cstructs = [m.camera_struct(c) for c in cams]
+    stream = torch.cuda.Stream(device=local)
+    out = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # Size the workspace on every pose (checked renders), and count the
+    # included (pixel, Gaussian) pairs per pose for the roofline.
+    cnt = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    hits = []
+    for c in cstructs:
+        m.mgs_render_checked(r.ws, h, c, opts, out, None, cnt, stream)
+        hits.append(int(cnt.sum(dtype=torch.int64)))
+    _, pairs = m.mgs_workspace_sync(r.ws, stream)
+
+    def sweep():
+        for c in cstructs:
+            m.mgs_render(r.ws, h, c, opts, out, None, None, stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        with torch.cuda.stream(stream):
+            sweep()
+    barrier()
+    st, _ = m.mgs_workspace_sync(r.ws, stream)
+
+    step_ms = []
+    m.mgs_workspace_stage_times(r.ws, stream)      # reset
+    m.mgs_workspace_set_timing(r.ws, True)         # events around each stage
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sweep()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        barrier()
+    clocks = clk.summary()
+    stage_ms, timed_frames = m.mgs_workspace_stage_times(r.ws, stream)
+    m.mgs_workspace_set_timing(r.ws, False)
+    st, _ = m.mgs_workspace_sync(r.ws, stream, allow_overflow=True)
+    if st != m.MGS_OK:
+        raise RuntimeError("tile-list overflow inside the timed region")
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    frames = N_POSES * args.steps * world
+    fps = frames / (total_ms / 1000.0)
+
+    stage_per_frame = [x / max(timed_frames, 1) for x in stage_ms]
+    rast = {"ms_per_frame": stage_per_frame[2]}
+
+    # ---- end to end: host image buffers (pinned), D2H inside the timed region
+    host = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c in cstructs:
+            m.mgs_render_to_host(r.ws, h, c, opts, host, stream)
+        stream.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    e2e_total = sum(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_fps = frames / (e2e_total / 1000.0)
+
+    peaks, peaks_kind = _peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    mean_hits = sum(hits) / len(hits)
+    # algorithmic work of the rasteriser: 16 FP32 lane-ops per included pair
+    # (7 for the quadratic form, 9 for alpha and the A/B/T updates) + 1 MUFU
+    achieved = 16.0 * mean_hits / (rast["ms_per_frame"] / 1000.0) / 1e12
+    peak_alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "raster_traffic.json")
+    if os.path.exists(prof):
+        traffic = json.load(open(prof)).get("bytes_per_launch")
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": fps, "unit": "FPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "unbounded_600k_fp16_mlp_1600x1063_orbit64",
+                       "gaussians": scene.n, "resolution": [W, H], "poses_per_step": N_POSES,
+                       "attrs": "fp16", "mlp": "bf16 22-64-64-5", "parallelism": "replicas",
+                       "l2": "flushed (512 MB write) between timed steps",
+                       "pairs_per_frame_max": pairs, "hits_per_frame_mean": mean_hits},
+            "e2e": {"value": e2e_fps, "unit": "FPS",
+                    "h2d_bytes_per_step": N_POSES * 68,
+                    "d2h_bytes_per_step": N_POSES * H * W * 12},
+            "roofline": {"bound": "alu", "kernel": "k_raster",
+                         "achieved": achieved, "peak": peak_alu, "unit": "T FP32-lane-op/s",
+                         "frac": achieved / peak_alu, "traffic": traffic,
+                         "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median "
+                                        f"SM clock sampled in the timed region)",
+                         "raster_ms_per_frame": rast["ms_per_frame"],
+                         "stage_ms_per_frame": {"preprocess_mlp": stage_per_frame[0],
+                                                "binning": stage_per_frame[1],
+                                                "raster": stage_per_frame[2]}},
+            "gpu_launches": 4 * N_POSES * args.steps,
+            "clocks": clocks,
+            "peaks": peaks_kind,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            cb = cpu_baseline_sample()
+            cb.pop("seconds", None)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line), flush=True)
+    r.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

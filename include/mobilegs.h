@@ -1,0 +1,207 @@
+/*
+ * mobilegs.h -- C-ABI of the GB300 (sm_103a) sort-free Gaussian renderer.
+ *
+ * The renderer computes the depth-aware, order-independent image of Mobile-GS
+ * (arxiv 2603.11531):
+ *
+ *   C(p) = (1 - T) * sum_i c_i a_i w_i / sum_i a_i w_i + T * c_bg      (Sec. 3.1, Eq. 2)
+ *   T    = prod_i (1 - a_i),   a_i = o_i exp(-1/2 dx^T Sigma_i^-1 dx)  (Sec. 3.1, Eq. 2)
+ *   w_i  = phi_i^2 + phi_i / d_i^2 + exp(s_max / d_i)                 (Sec. 3.1, Eq. 3)
+ *   phi_i, o_i = ReLU(MLP_phi F), sigmoid(MLP_o F),
+ *   F = MLP_f(P_i, s_i, r_i, Y_i)                                      (Sec. 3.1, Eq. 4)
+ *
+ * with c_i the first-order spherical-harmonics colour (Sec. 3.2) and the
+ * Gaussians (mu, Sigma = R S S^T R^T, o, Y) projected as in App. B.  The sums
+ * commute (Sec. 2, discussion of Eq. 1), so no depth sort is done: Gaussians
+ * are binned into 16x16-pixel tiles by tile only, and every pixel
+ * accumulates its tile's list in whatever order it is stored.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns an mgs_status; nothing throws across the ABI.
+ *     On failure, mgs_last_error() returns a message for the calling thread.
+ *   - Device pointers are CUDA global-memory pointers on the context's
+ *     device; host pointers are ordinary (pageable or pinned) memory.
+ *   - Output buffers are owned by the caller; the library never frees them.
+ *     Scenes and workspaces own their device memory until destroyed.
+ *   - Rendering calls are asynchronous on the given stream (NULL = the legacy
+ *     default stream).  Arguments are checked on the host before any launch.
+ *     Errors that only the device can see (tile-list capacity overflow) are
+ *     recorded in the workspace and reported by mgs_workspace_sync().
+ *   - A workspace holds the per-frame scratch (projected Gaussians, tile
+ *     lists).  Renders that share a workspace must be ordered on one stream;
+ *     concurrent renders need one workspace each.
+ */
+#ifndef MOBILEGS_H
+#define MOBILEGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (same type, declared here so that this header needs no CUDA
+ * headers). */
+typedef struct CUstream_st *mgs_stream;
+
+typedef enum {
+    MGS_OK = 0,
+    MGS_ERR_INVALID_ARG = 1,  /* bad pointer, size, camera or option */
+    MGS_ERR_OOM = 2,          /* device allocation failed */
+    MGS_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+    MGS_ERR_OVERFLOW = 4,     /* a render needed more tile-list capacity than
+                                 its workspace had; its image is invalid */
+    MGS_ERR_TIMEOUT = 5,      /* a bounded wait gave up */
+    MGS_ERR_BUSY = 6,         /* resource in use (e.g. admission refused) */
+    MGS_ERR_NOT_READY = 7     /* work still in flight */
+} mgs_status;
+
+enum { MGS_PREC_FP32 = 0, MGS_PREC_FP16 = 1 };
+
+/* Render flags (mgs_render_opts.flags). */
+enum {
+    MGS_FLAG_NO_CULL = 1u  /* debug: skip the conservative per-warp culling of
+                              tile lists (the image must not change) */
+};
+
+typedef struct mgs_ctx_s *mgs_ctx;
+typedef struct mgs_scene_s *mgs_scene;
+typedef struct mgs_workspace_s *mgs_workspace;
+
+/* Gaussian record: 24 elements of the stored precision per Gaussian (App. B
+ * parameters; activated values):
+ *   [0..2]  mean mu (world)          [3..5]  scale s (> 0, per local axis)
+ *   [6..9]  quaternion (w, x, y, z), any norm > 0 (normalised by the renderer)
+ *   [10]    opacity o in [0, 1]      [11..22] SH coefficients, coefficient-
+ *                                          major: Y0 rgb, Y1 rgb, Y2 rgb, Y3 rgb
+ *   [23]    ignored (padding)
+ * Enhancement MLP (Eq. 4), optional: w1 [64][22], w2 [64][64], w3 [5][64]
+ * as BF16 bit patterns, row-major [out][in]; biases b1 [64], b2 [64], b3 [5]
+ * FP32.  Head rows: phi, o, d_r, d_g, d_b (the last three are an optional
+ * colour residual).  MLP input: [P(3), s(3), normalised q(4), Y(12)]. */
+typedef struct {
+    int64_t n;              /* number of Gaussians, >= 0 */
+    int32_t precision;      /* MGS_PREC_FP32 or MGS_PREC_FP16 */
+    int32_t attrs_on_device;/* 1: attrs is a device pointer; 0: host */
+    const void *attrs;      /* n x 24 elements, 16-byte aligned if on device */
+    const uint16_t *mlp_w1; /* host pointers; all NULL = scene has no MLP */
+    const float *mlp_b1;
+    const uint16_t *mlp_w2;
+    const float *mlp_b2;
+    const uint16_t *mlp_w3;
+    const float *mlp_b3;
+} mgs_scene_desc;
+
+/* Pinhole camera, world->camera (R row-major, t), OpenCV axes (x right,
+ * y down, z forward).  Pixel (x, y) has its centre at (x + 0.5, y + 0.5). */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;   /* 1 .. 16384 */
+    float znear;             /* Gaussians with view z <= znear are culled */
+} mgs_camera;
+
+typedef struct {
+    int32_t use_mlp;          /* 0: phi = 1, o = stored opacity; 1: Eq. 4 */
+    int32_t mlp_rgb_residual; /* 1: add the MLP's colour head before clamping */
+    float bg[3];              /* c_bg */
+    uint32_t flags;           /* MGS_FLAG_* */
+} mgs_render_opts;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`. */
+mgs_status mgs_ctx_create(int32_t device, mgs_ctx *out);
+mgs_status mgs_ctx_destroy(mgs_ctx ctx);
+
+/* Static facts of the context's device: SM count, free and total memory. */
+mgs_status mgs_ctx_info(mgs_ctx ctx, int32_t *sm_count, int64_t *free_bytes,
+                        int64_t *total_bytes);
+
+/* ---- scenes (App. B parameters, resident in device memory) --------------- */
+
+/* Copy a scene into library-owned device memory (stream-ordered on
+ * `stream`; the copy has completed when the call returns, so host buffers
+ * may be reused at once).  MLP weights are repacked for the tensor cores. */
+mgs_status mgs_load_scene(mgs_ctx ctx, const mgs_scene_desc *desc,
+                          mgs_stream stream, mgs_scene *out);
+mgs_status mgs_unload_scene(mgs_scene scene);
+/* Device bytes held by the scene. */
+int64_t mgs_scene_bytes(mgs_scene scene);
+
+/* ---- workspaces (per-frame scratch) -------------------------------------- */
+
+mgs_status mgs_workspace_create(mgs_ctx ctx, mgs_workspace *out);
+mgs_status mgs_workspace_destroy(mgs_workspace ws);
+/* Pre-size the scratch for n Gaussians, a width x height image and `pairs`
+ * (tile, Gaussian) intersections, so that later renders allocate nothing. */
+mgs_status mgs_workspace_reserve(mgs_workspace ws, int64_t n, int32_t width,
+                                 int32_t height, int64_t pairs);
+/* Device bytes held by the workspace. */
+int64_t mgs_workspace_bytes(mgs_workspace ws);
+/* Wait for `stream`, then report renders since the previous sync:
+ * MGS_ERR_OVERFLOW if any ran out of tile-list capacity (the workspace is then
+ * grown so that a repeat succeeds).  *pairs_out (nullable) = the largest
+ * number of (tile, Gaussian) pairs any of them needed. */
+mgs_status mgs_workspace_sync(mgs_workspace ws, mgs_stream stream,
+                              int64_t *pairs_out);
+
+/* Per-stage device timing (the runtime breakdown the paper reports in
+ * Fig. 2 and Fig. 6).  While enabled, every render on the workspace records
+ * CUDA events on its stream around (0) preprocessing incl. the MLP,
+ * (1) binning (count reset, scan, scatter) and (2) rasterisation. */
+mgs_status mgs_workspace_set_timing(mgs_workspace ws, int32_t enable);
+/* Wait for `stream`; ms[0..2] = summed stage times in milliseconds of the
+ * renders timed since the previous call, *frames = their number.  Resets. */
+mgs_status mgs_workspace_stage_times(mgs_workspace ws, mgs_stream stream,
+                                     double ms[3], int64_t *frames);
+
+/* ---- rendering (Sec. 3.1, Eq. 2-4) --------------------------------------- */
+
+/* Render one view.  out_rgb: device, height x width x 3 FP32 (row-major, RGB
+ * interleaved).  out_aux (nullable): device, 5 x height x width FP32 planes
+ * (A_r, A_g, A_b, B, T) with A = sum c a w, B = sum a w, T = prod (1 - a),
+ * the quantities the backward pass needs.  out_count (nullable): device,
+ * height x width int32, number of Gaussians included at each pixel.
+ * Asynchronous; a capacity overflow is reported by mgs_workspace_sync(). */
+mgs_status mgs_render(mgs_workspace ws, mgs_scene scene, const mgs_camera *cam,
+                      const mgs_render_opts *opts, float *out_rgb,
+                      float *out_aux, int32_t *out_count, mgs_stream stream);
+
+/* mgs_render, then mgs_workspace_sync, repeated once after growing the
+ * workspace if the first attempt overflowed.  Synchronous. */
+mgs_status mgs_render_checked(mgs_workspace ws, mgs_scene scene,
+                              const mgs_camera *cam,
+                              const mgs_render_opts *opts, float *out_rgb,
+                              float *out_aux, int32_t *out_count,
+                              mgs_stream stream);
+
+/* End-to-end render into HOST memory: renders into a workspace-owned device
+ * image and copies it to host_rgb (height x width x 3 FP32; pinned memory
+ * gives an asynchronous copy).  Asynchronous on `stream` like mgs_render. */
+mgs_status mgs_render_to_host(mgs_workspace ws, mgs_scene scene,
+                              const mgs_camera *cam,
+                              const mgs_render_opts *opts, float *host_rgb,
+                              mgs_stream stream);
+
+/* Tile lists of the workspace's most recent render, for tests.  Waits for
+ * `stream`, then reports n_tiles and n_pairs (= offsets[n_tiles]); if both
+ * output buffers are non-NULL it also copies offsets [n_tiles + 1] and
+ * gids [n_pairs] into them (caller-owned device memory).  Each tile's
+ * Gaussian indices are in unspecified order.  MGS_ERR_OVERFLOW if that render
+ * overflowed (its lists are incomplete). */
+mgs_status mgs_tile_lists(mgs_workspace ws, mgs_stream stream, int64_t *n_tiles,
+                          int64_t *n_pairs, uint32_t *offsets_out,
+                          uint32_t *gids_out);
+
+/* ---- diagnostics --------------------------------------------------------- */
+
+const char *mgs_last_error(void);
+const char *mgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOBILEGS_H */

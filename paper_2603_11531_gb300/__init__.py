@@ -1,0 +1,354 @@
+"""Python binding of the GB300 sort-free Gaussian renderer (libmobilegs.so).
+
+Argument marshalling only: every step of a render runs in the CUDA kernels
+behind the C-ABI (include/mobilegs.h).  The functions mirror the C entry
+points by name; `Renderer` bundles a context, a workspace and torch output
+buffers for convenience.  There is no CPU fallback: if the compiled library
+is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmobilegs.so")
+_lib = None
+_lock = threading.Lock()
+
+MGS_OK = 0
+MGS_ERR_INVALID_ARG = 1
+MGS_ERR_OOM = 2
+MGS_ERR_CUDA = 3
+MGS_ERR_OVERFLOW = 4
+MGS_ERR_TIMEOUT = 5
+MGS_ERR_BUSY = 6
+MGS_ERR_NOT_READY = 7
+MGS_PREC_FP32 = 0
+MGS_PREC_FP16 = 1
+MGS_FLAG_NO_CULL = 1
+
+# Every entry point declared in include/mobilegs.h.
+EXPORTS = (
+    "mgs_ctx_create", "mgs_ctx_destroy", "mgs_ctx_info", "mgs_load_scene",
+    "mgs_unload_scene", "mgs_scene_bytes", "mgs_workspace_create", "mgs_workspace_destroy",
+    "mgs_workspace_reserve", "mgs_workspace_bytes", "mgs_workspace_sync", "mgs_render",
+    "mgs_render_checked", "mgs_render_to_host", "mgs_tile_lists", "mgs_last_error",
+    "mgs_version", "mgs_workspace_set_timing", "mgs_workspace_stage_times",
+)
+
+
+class MGSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mobilegs status {status}: {msg}")
+        self.status = status
+
+
+class mgs_camera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("znear", ctypes.c_float)]
+
+
+class mgs_render_opts(ctypes.Structure):
+    _fields_ = [("use_mlp", ctypes.c_int32), ("mlp_rgb_residual", ctypes.c_int32),
+                ("bg", ctypes.c_float * 3), ("flags", ctypes.c_uint32)]
+
+
+class mgs_scene_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("attrs_on_device", ctypes.c_int32), ("attrs", ctypes.c_void_p),
+                ("mlp_w1", ctypes.c_void_p), ("mlp_b1", ctypes.c_void_p),
+                ("mlp_w2", ctypes.c_void_p), ("mlp_b2", ctypes.c_void_p),
+                ("mlp_w3", ctypes.c_void_p), ("mlp_b3", ctypes.c_void_p)]
+
+
+def lib():
+    """Load libmobilegs.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it first "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(LIB_PATH)
+            P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            sig = {
+                "mgs_ctx_create": ([I32, PP], I32),
+                "mgs_ctx_destroy": ([P], I32),
+                "mgs_ctx_info": ([P, ctypes.POINTER(I32), ctypes.POINTER(I64), ctypes.POINTER(I64)], I32),
+                "mgs_load_scene": ([P, ctypes.POINTER(mgs_scene_desc), P, PP], I32),
+                "mgs_unload_scene": ([P], I32),
+                "mgs_scene_bytes": ([P], I64),
+                "mgs_workspace_create": ([P, PP], I32),
+                "mgs_workspace_destroy": ([P], I32),
+                "mgs_workspace_reserve": ([P, I64, I32, I32, I64], I32),
+                "mgs_workspace_bytes": ([P], I64),
+                "mgs_workspace_sync": ([P, P, ctypes.POINTER(I64)], I32),
+                "mgs_render": ([P, P, ctypes.POINTER(mgs_camera), ctypes.POINTER(mgs_render_opts),
+                                P, P, P, P], I32),
+                "mgs_render_checked": ([P, P, ctypes.POINTER(mgs_camera),
+                                        ctypes.POINTER(mgs_render_opts), P, P, P, P], I32),
+                "mgs_render_to_host": ([P, P, ctypes.POINTER(mgs_camera),
+                                        ctypes.POINTER(mgs_render_opts), P, P], I32),
+                "mgs_tile_lists": ([P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P], I32),
+                "mgs_workspace_set_timing": ([P, I32], I32),
+                "mgs_workspace_stage_times": ([P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], I32),
+                "mgs_last_error": ([], ctypes.c_char_p),
+                "mgs_version": ([], ctypes.c_char_p),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(status: int, allow=()) -> int:
+    if status != MGS_OK and status not in allow:
+        raise MGSError(status, lib().mgs_last_error().decode())
+    return status
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def camera_struct(cam) -> mgs_camera:
+    c = mgs_camera()
+    R = np.asarray(cam.R, np.float32).reshape(9)
+    t = np.asarray(cam.t, np.float32).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.fx, c.fy, c.cx, c.cy = (float(v) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.znear = float(getattr(cam, "znear", 0.2))
+    return c
+
+
+def render_opts(use_mlp=False, rgb_residual=False, bg=(0.0, 0.0, 0.0), flags=0) -> mgs_render_opts:
+    o = mgs_render_opts()
+    o.use_mlp = int(bool(use_mlp))
+    o.mlp_rgb_residual = int(bool(rgb_residual))
+    for k in range(3):
+        o.bg[k] = float(bg[k])
+    o.flags = int(flags)
+    return o
+
+
+# ---- thin wrappers with the C names ------------------------------------------
+
+def mgs_ctx_create(device: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib().mgs_ctx_create(device, ctypes.byref(h)))
+    return h
+
+
+def mgs_ctx_destroy(ctx):
+    _check(lib().mgs_ctx_destroy(ctx))
+
+
+def mgs_ctx_info(ctx):
+    sm, fr, tot = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().mgs_ctx_info(ctx, ctypes.byref(sm), ctypes.byref(fr), ctypes.byref(tot)))
+    return sm.value, fr.value, tot.value
+
+
+def mgs_load_scene(ctx, attrs, mlp=None, stream=None):
+    """attrs: (N, 24) float32/float16 numpy array or CUDA torch tensor."""
+    d = mgs_scene_desc()
+    keep = []
+    on_dev = hasattr(attrs, "is_cuda") and attrs.is_cuda
+    if on_dev:
+        import torch
+        a = attrs.contiguous()
+        prec = MGS_PREC_FP16 if a.dtype == torch.float16 else MGS_PREC_FP32
+        if a.dtype not in (torch.float16, torch.float32):
+            raise TypeError("attrs must be float16 or float32")
+    else:
+        a = np.ascontiguousarray(attrs)
+        if a.dtype not in (np.float16, np.float32):
+            raise TypeError("attrs must be float16 or float32")
+        prec = MGS_PREC_FP16 if a.dtype == np.float16 else MGS_PREC_FP32
+    if a.ndim != 2 or a.shape[1] != 24:
+        raise ValueError("attrs must have shape (N, 24)")
+    keep.append(a)
+    d.n = int(a.shape[0])
+    d.precision = prec
+    d.attrs_on_device = int(on_dev)
+    d.attrs = _ptr(a)
+    if mlp is not None:
+        arrs = [np.ascontiguousarray(mlp.w1, np.uint16), np.ascontiguousarray(mlp.b1, np.float32),
+                np.ascontiguousarray(mlp.w2, np.uint16), np.ascontiguousarray(mlp.b2, np.float32),
+                np.ascontiguousarray(mlp.w3, np.uint16), np.ascontiguousarray(mlp.b3, np.float32)]
+        assert arrs[0].shape == (64, 22) and arrs[2].shape == (64, 64) and arrs[4].shape == (5, 64)
+        keep += arrs
+        (d.mlp_w1, d.mlp_b1, d.mlp_w2, d.mlp_b2, d.mlp_w3, d.mlp_b3) = [x.ctypes.data for x in arrs]
+    h = ctypes.c_void_p()
+    _check(lib().mgs_load_scene(ctx, ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def mgs_unload_scene(scene):
+    _check(lib().mgs_unload_scene(scene))
+
+
+def mgs_scene_bytes(scene) -> int:
+    return lib().mgs_scene_bytes(scene)
+
+
+def mgs_workspace_create(ctx):
+    h = ctypes.c_void_p()
+    _check(lib().mgs_workspace_create(ctx, ctypes.byref(h)))
+    return h
+
+
+def mgs_workspace_destroy(ws):
+    _check(lib().mgs_workspace_destroy(ws))
+
+
+def mgs_workspace_reserve(ws, n, width, height, pairs):
+    _check(lib().mgs_workspace_reserve(ws, int(n), int(width), int(height), int(pairs)))
+
+
+def mgs_workspace_bytes(ws) -> int:
+    return lib().mgs_workspace_bytes(ws)
+
+
+def mgs_workspace_sync(ws, stream=None, allow_overflow=False):
+    pairs = ctypes.c_int64()
+    st = lib().mgs_workspace_sync(ws, _stream(stream), ctypes.byref(pairs))
+    _check(st, allow=(MGS_ERR_OVERFLOW,) if allow_overflow else ())
+    return st, pairs.value
+
+
+def mgs_render(ws, scene, cam, opts, out_rgb, out_aux=None, out_count=None, stream=None):
+    c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    _check(lib().mgs_render(ws, scene, ctypes.byref(c), ctypes.byref(opts), _ptr(out_rgb),
+                            _ptr(out_aux), _ptr(out_count), _stream(stream)))
+
+
+def mgs_render_checked(ws, scene, cam, opts, out_rgb, out_aux=None, out_count=None, stream=None):
+    c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    _check(lib().mgs_render_checked(ws, scene, ctypes.byref(c), ctypes.byref(opts), _ptr(out_rgb),
+                                    _ptr(out_aux), _ptr(out_count), _stream(stream)))
+
+
+def mgs_render_to_host(ws, scene, cam, opts, host_rgb, stream=None):
+    c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    _check(lib().mgs_render_to_host(ws, scene, ctypes.byref(c), ctypes.byref(opts),
+                                    _ptr(host_rgb), _stream(stream)))
+
+
+def mgs_tile_lists(ws, offsets_out=None, gids_out=None, stream=None):
+    """(n_tiles, n_pairs) of the workspace's last render; copies the lists
+    into the given device tensors when both are passed."""
+    n, k = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().mgs_tile_lists(ws, _stream(stream), ctypes.byref(n), ctypes.byref(k),
+                                _ptr(offsets_out), _ptr(gids_out)))
+    return n.value, k.value
+
+
+def mgs_workspace_set_timing(ws, enable: bool):
+    _check(lib().mgs_workspace_set_timing(ws, int(bool(enable))))
+
+
+def mgs_workspace_stage_times(ws, stream=None):
+    """(ms[3], frames): summed (preprocess+MLP, binning, rasterise) times."""
+    ms = (ctypes.c_double * 3)()
+    fr = ctypes.c_int64()
+    _check(lib().mgs_workspace_stage_times(ws, _stream(stream), ms, ctypes.byref(fr)))
+    return [ms[0], ms[1], ms[2]], fr.value
+
+
+def mgs_version() -> str:
+    return lib().mgs_version().decode()
+
+
+# ---- convenience -------------------------------------------------------------
+
+class Renderer:
+    """One context + one workspace on a CUDA device; outputs are torch tensors."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.ctx = mgs_ctx_create(device)
+        self.ws = mgs_workspace_create(self.ctx)
+        self._scenes = []
+
+    def load_scene(self, scene_or_attrs, mlp=None, stream=None):
+        attrs = getattr(scene_or_attrs, "attrs", scene_or_attrs)
+        if mlp is None:
+            mlp = getattr(scene_or_attrs, "mlp", None)
+        h = mgs_load_scene(self.ctx, attrs, mlp, stream)
+        self._scenes.append(h)
+        return h
+
+    def unload_scene(self, h):
+        mgs_unload_scene(h)
+        self._scenes = [s for s in self._scenes if s.value != h.value]
+
+    def render(self, scene, cam, use_mlp=False, rgb_residual=False, bg=(0.0, 0.0, 0.0),
+               aux=False, count=False, flags=0, stream=None, checked=True):
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        H, W = int(cam.height), int(cam.width)
+        rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        a = torch.empty((5, H, W), dtype=torch.float32, device=dev) if aux else None
+        c = torch.empty((H, W), dtype=torch.int32, device=dev) if count else None
+        opts = render_opts(use_mlp, rgb_residual, bg, flags)
+        fn = mgs_render_checked if checked else mgs_render
+        fn(self.ws, scene, cam, opts, rgb, a, c, stream)
+        return {"rgb": rgb, "aux": a, "count": c}
+
+    def tile_lists(self, stream=None):
+        """Copies of the last render's tile lists as numpy arrays (offsets, gids)."""
+        torch = self.torch
+        n, k = mgs_tile_lists(self.ws, stream=stream)
+        dev = torch.device("cuda", self.device)
+        off = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        gids = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+        mgs_tile_lists(self.ws, off, gids, stream=stream)
+        return (off.cpu().numpy().view(np.uint32).astype(np.int64),
+                gids[:k].cpu().numpy().view(np.uint32).astype(np.int64))
+
+    def close(self):
+        for s in self._scenes:
+            mgs_unload_scene(s)
+        self._scenes = []
+        if self.ws is not None:
+            mgs_workspace_destroy(self.ws)
+            self.ws = None
+        if self.ctx is not None:
+            mgs_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

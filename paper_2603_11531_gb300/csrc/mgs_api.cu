@@ -1,0 +1,550 @@
+// Host side of the C-ABI declared in include/mobilegs.h: argument checks,
+// device memory of scenes and workspaces, and the launch sequence of a render
+// (preprocess -> scan -> scatter -> rasterise).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <array>
+#include <vector>
+
+#include "mgs_internal.cuh"
+
+using namespace mgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+mgs_status fail(mgs_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+mgs_status cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(MGS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(MGS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+cudaError_t dev_alloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+template <class T>
+void dev_free(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
+
+}  // namespace
+
+struct mgs_ctx_s {
+    int device = 0;
+    int sm_count = 0;
+};
+
+struct mgs_scene_s {
+    mgs_ctx ctx = nullptr;
+    int64_t n = 0;
+    int precision = MGS_PREC_FP32;
+    void *attrs = nullptr;
+    bool has_mlp = false;
+    unsigned char *mlp_blob = nullptr;  // packed weights + biases
+    DevMLP mlp{};
+    int64_t bytes = 0;
+};
+
+struct mgs_workspace_s {
+    mgs_ctx ctx = nullptr;
+    int64_t n_cap = 0;
+    int64_t tiles_cap = 0;
+    uint64_t pair_cap = 0;
+    int64_t img_cap = 0;
+    ProjRec *rec = nullptr;
+    uint2 *rect = nullptr;
+    uint32_t *tile_count = nullptr;
+    uint32_t *tile_offsets = nullptr;
+    uint32_t *tile_cursor = nullptr;
+    uint32_t *gids = nullptr;
+    float *img = nullptr;
+    DevStatus *status = nullptr;
+    int64_t last_tiles = 0;
+    uint64_t grow_hint = 0;  // pairs needed by an overflowed render
+    bool timing = false;
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<std::array<cudaEvent_t, 4>> pending;  // per timed render
+};
+
+namespace {
+
+int64_t ws_bytes(const mgs_workspace_s *w) {
+    return w->n_cap * (int64_t)(sizeof(ProjRec) + sizeof(uint2)) +
+           w->tiles_cap * 3 * (int64_t)sizeof(uint32_t) + (int64_t)w->pair_cap * 4 +
+           w->img_cap * 12 + (int64_t)sizeof(DevStatus);
+}
+
+mgs_status ws_ensure(mgs_workspace_s *w, int64_t n, int64_t tiles, uint64_t pairs) {
+    cudaError_t e;
+    if (n > w->n_cap) {
+        dev_free(w->rec);
+        dev_free(w->rect);
+        w->n_cap = 0;
+        if ((e = dev_alloc(&w->rec, (size_t)n)) != cudaSuccess) return cuda_fail(e, "workspace");
+        if ((e = dev_alloc(&w->rect, (size_t)n)) != cudaSuccess) return cuda_fail(e, "workspace");
+        w->n_cap = n;
+    }
+    if (tiles + 1 > w->tiles_cap) {
+        dev_free(w->tile_count);
+        dev_free(w->tile_offsets);
+        dev_free(w->tile_cursor);
+        w->tiles_cap = 0;
+        const size_t t = (size_t)tiles + 1;
+        if ((e = dev_alloc(&w->tile_count, t)) != cudaSuccess) return cuda_fail(e, "workspace");
+        if ((e = dev_alloc(&w->tile_offsets, t)) != cudaSuccess) return cuda_fail(e, "workspace");
+        if ((e = dev_alloc(&w->tile_cursor, t)) != cudaSuccess) return cuda_fail(e, "workspace");
+        w->tiles_cap = (int64_t)t;
+    }
+    if (pairs > w->pair_cap) {
+        if (pairs > 0xFFFFFFFFull) pairs = 0xFFFFFFFFull;
+        dev_free(w->gids);
+        w->pair_cap = 0;
+        if ((e = dev_alloc(&w->gids, (size_t)pairs)) != cudaSuccess) return cuda_fail(e, "workspace");
+        w->pair_cap = pairs;
+    }
+    if (!w->status) {
+        if ((e = dev_alloc(&w->status, 1)) != cudaSuccess) return cuda_fail(e, "workspace");
+        if ((e = cudaMemset(w->status, 0, sizeof(DevStatus))) != cudaSuccess)
+            return cuda_fail(e, "workspace");
+    }
+    return MGS_OK;
+}
+
+mgs_status check_camera(const mgs_camera *c) {
+    if (!c) return fail(MGS_ERR_INVALID_ARG, "camera is NULL");
+    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
+        return fail(MGS_ERR_INVALID_ARG, "image size %dx%d outside 1..16384", c->width, c->height);
+    if (!finite_pos(c->fx) || !finite_pos(c->fy))
+        return fail(MGS_ERR_INVALID_ARG, "focal lengths must be finite and > 0");
+    if (!std::isfinite(c->cx) || !std::isfinite(c->cy) || !std::isfinite(c->znear))
+        return fail(MGS_ERR_INVALID_ARG, "principal point and znear must be finite");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(c->R[i])) return fail(MGS_ERR_INVALID_ARG, "R must be finite");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(c->t[i])) return fail(MGS_ERR_INVALID_ARG, "t must be finite");
+    return MGS_OK;
+}
+
+DevCamera to_dev(const mgs_camera *c) {
+    DevCamera d;
+    memcpy(d.R, c->R, sizeof d.R);
+    memcpy(d.t, c->t, sizeof d.t);
+    d.fx = c->fx;
+    d.fy = c->fy;
+    d.cx = c->cx;
+    d.cy = c->cy;
+    d.width = c->width;
+    d.height = c->height;
+    d.znear = c->znear;
+    d.tiles_x = (c->width + kTile - 1) / kTile;
+    d.tiles_y = (c->height + kTile - 1) / kTile;
+    return d;
+}
+
+uint64_t default_pairs(int64_t n) {
+    uint64_t p = (uint64_t)n * 24u;
+    return p < (1u << 20) ? (1u << 20) : p;
+}
+
+mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
+                       const mgs_render_opts *opts, float *out_rgb, float *out_aux,
+                       int32_t *out_count, cudaStream_t stream) {
+    if (!w || !s) return fail(MGS_ERR_INVALID_ARG, "workspace or scene is NULL");
+    if (w->ctx != s->ctx) return fail(MGS_ERR_INVALID_ARG, "scene and workspace belong to different contexts");
+    mgs_status st = check_camera(cam);
+    if (st != MGS_OK) return st;
+    if (!opts) return fail(MGS_ERR_INVALID_ARG, "opts is NULL");
+    if (!out_rgb) return fail(MGS_ERR_INVALID_ARG, "out_rgb is NULL");
+    if (opts->use_mlp && !s->has_mlp)
+        return fail(MGS_ERR_INVALID_ARG, "use_mlp requested but the scene has no MLP weights");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(opts->bg[k])) return fail(MGS_ERR_INVALID_ARG, "bg must be finite");
+    DeviceGuard g(w->ctx->device);
+    if (!g.ok) return fail(MGS_ERR_CUDA, "cannot select device %d", w->ctx->device);
+
+    const DevCamera dc = to_dev(cam);
+    const int64_t T = (int64_t)dc.tiles_x * dc.tiles_y;
+    uint64_t want = w->pair_cap ? w->pair_cap : default_pairs(s->n);
+    if (w->grow_hint > want) want = w->grow_hint;
+    st = ws_ensure(w, s->n, T, want);
+    if (st != MGS_OK) return st;
+
+    RenderArgs a{};
+    a.attrs = s->attrs;
+    a.n = s->n;
+    a.precision = s->precision;
+    a.use_mlp = opts->use_mlp ? 1 : 0;
+    a.rgb_residual = (opts->use_mlp && opts->mlp_rgb_residual) ? 1 : 0;
+    a.mlp = s->mlp;
+    a.cam = dc;
+    a.bg[0] = opts->bg[0];
+    a.bg[1] = opts->bg[1];
+    a.bg[2] = opts->bg[2];
+    a.flags = opts->flags;
+    a.rec = w->rec;
+    a.rect = w->rect;
+    a.tile_count = w->tile_count;
+    a.tile_offsets = w->tile_offsets;
+    a.tile_cursor = w->tile_cursor;
+    a.gids = w->gids;
+    a.capacity = w->pair_cap;
+    a.status = w->status;
+    a.out_rgb = out_rgb;
+    a.out_aux = out_aux;
+    a.out_count = out_count;
+
+    std::array<cudaEvent_t, 4> ev{};
+    cudaError_t e = cudaSuccess;
+    if (w->timing) {
+        for (auto &x : ev) {
+            if (w->event_pool.empty()) {
+                if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(e, "event");
+            } else {
+                x = w->event_pool.back();
+                w->event_pool.pop_back();
+            }
+        }
+        cudaEventRecord(ev[0], stream);
+    }
+    if (s->n > 0 && (e = launch_preprocess(a, w->ctx->sm_count, stream, w->tile_count, T)) != cudaSuccess)
+        return cuda_fail(e, "preprocess launch");
+    if (s->n == 0 && (e = cudaMemsetAsync(w->tile_count, 0, (size_t)T * 4, stream)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    if (w->timing) cudaEventRecord(ev[1], stream);
+    if ((e = launch_binning(a, stream)) != cudaSuccess) return cuda_fail(e, "binning launch");
+    if (w->timing) cudaEventRecord(ev[2], stream);
+    if ((e = launch_raster(a, stream)) != cudaSuccess) return cuda_fail(e, "raster launch");
+    if (w->timing) {
+        cudaEventRecord(ev[3], stream);
+        w->pending.push_back(ev);
+    }
+    w->last_tiles = T;
+    return MGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mgs_last_error(void) { return g_err.c_str(); }
+const char *mgs_version(void) { return "mobilegs-gb300 0.1 (sm_103a)"; }
+
+mgs_status mgs_ctx_create(int32_t device, mgs_ctx *out) {
+    if (!out) return fail(MGS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(MGS_ERR_INVALID_ARG, "no CUDA device %d", device);
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess)
+        return cuda_fail(e, "cudaGetDeviceProperties");
+    if (prop.major * 10 + prop.minor < 100)
+        return fail(MGS_ERR_INVALID_ARG, "device %d is sm_%d%d; this library is built for sm_103a",
+                    device, prop.major, prop.minor);
+    mgs_ctx c = new mgs_ctx_s;
+    c->device = device;
+    c->sm_count = prop.multiProcessorCount;
+    *out = c;
+    return MGS_OK;
+}
+
+mgs_status mgs_ctx_destroy(mgs_ctx ctx) {
+    delete ctx;
+    return MGS_OK;
+}
+
+mgs_status mgs_ctx_info(mgs_ctx ctx, int32_t *sm_count, int64_t *free_bytes, int64_t *total_bytes) {
+    if (!ctx) return fail(MGS_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    size_t fr = 0, tot = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    if (sm_count) *sm_count = ctx->sm_count;
+    if (free_bytes) *free_bytes = (int64_t)fr;
+    if (total_bytes) *total_bytes = (int64_t)tot;
+    return MGS_OK;
+}
+
+mgs_status mgs_load_scene(mgs_ctx ctx, const mgs_scene_desc *d, mgs_stream stream_, mgs_scene *out) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!ctx || !d || !out) return fail(MGS_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (d->n < 0 || d->n > (int64_t)1 << 31)
+        return fail(MGS_ERR_INVALID_ARG, "n = %lld outside 0..2^31", (long long)d->n);
+    if (d->precision != MGS_PREC_FP32 && d->precision != MGS_PREC_FP16)
+        return fail(MGS_ERR_INVALID_ARG, "unknown precision %d", d->precision);
+    if (d->n > 0 && !d->attrs) return fail(MGS_ERR_INVALID_ARG, "attrs is NULL");
+    const size_t elem = d->precision == MGS_PREC_FP16 ? 2 : 4;
+    if (d->attrs_on_device && (reinterpret_cast<uintptr_t>(d->attrs) & 15))
+        return fail(MGS_ERR_INVALID_ARG, "device attrs must be 16-byte aligned");
+    const bool any_mlp = d->mlp_w1 || d->mlp_b1 || d->mlp_w2 || d->mlp_b2 || d->mlp_w3 || d->mlp_b3;
+    const bool all_mlp = d->mlp_w1 && d->mlp_b1 && d->mlp_w2 && d->mlp_b2 && d->mlp_w3 && d->mlp_b3;
+    if (any_mlp && !all_mlp) return fail(MGS_ERR_INVALID_ARG, "MLP weights are partially given");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(MGS_ERR_CUDA, "cannot select device %d", ctx->device);
+
+    mgs_scene s = new mgs_scene_s;
+    s->ctx = ctx;
+    s->n = d->n;
+    s->precision = d->precision;
+    const size_t bytes = (size_t)d->n * kRec * elem;
+    cudaError_t e = cudaMalloc(&s->attrs, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "scene allocation");
+    }
+    if (bytes) {
+        e = cudaMemcpyAsync(s->attrs, d->attrs, bytes,
+                            d->attrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            stream);
+    }
+    s->bytes = (int64_t)bytes;
+    if (e == cudaSuccess && all_mlp) {
+        // pack: w1 [64][32] (cols 22.. zero), w2 [64][64], w3 [8][64] (rows 5.. zero)
+        const size_t n_w1 = kMlpHidden * kMlpK1, n_w2 = kMlpHidden * kMlpHidden,
+                     n_w3 = kMlpN3 * kMlpHidden;
+        const size_t off_w2 = n_w1 * 2, off_w3 = off_w2 + n_w2 * 2, off_b1 = off_w3 + n_w3 * 2,
+                     off_b2 = off_b1 + 64 * 4, off_b3 = off_b2 + 64 * 4, total = off_b3 + 8 * 4;
+        std::vector<unsigned char> blob(total, 0);
+        uint16_t *w1 = reinterpret_cast<uint16_t *>(blob.data());
+        uint16_t *w2 = reinterpret_cast<uint16_t *>(blob.data() + off_w2);
+        uint16_t *w3 = reinterpret_cast<uint16_t *>(blob.data() + off_w3);
+        float *b1 = reinterpret_cast<float *>(blob.data() + off_b1);
+        float *b2 = reinterpret_cast<float *>(blob.data() + off_b2);
+        float *b3 = reinterpret_cast<float *>(blob.data() + off_b3);
+        for (int r = 0; r < kMlpHidden; ++r)
+            for (int c = 0; c < kMlpIn; ++c) w1[r * kMlpK1 + c] = d->mlp_w1[r * kMlpIn + c];
+        memcpy(w2, d->mlp_w2, n_w2 * 2);
+        memcpy(w3, d->mlp_w3, (size_t)kMlpOut * kMlpHidden * 2);
+        memcpy(b1, d->mlp_b1, 64 * 4);
+        memcpy(b2, d->mlp_b2, 64 * 4);
+        memcpy(b3, d->mlp_b3, kMlpOut * 4);
+        e = cudaMalloc(&s->mlp_blob, total);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->mlp_blob, blob.data(), total, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        s->mlp.w1 = reinterpret_cast<const __nv_bfloat16 *>(s->mlp_blob);
+        s->mlp.w2 = reinterpret_cast<const __nv_bfloat16 *>(s->mlp_blob + off_w2);
+        s->mlp.w3 = reinterpret_cast<const __nv_bfloat16 *>(s->mlp_blob + off_w3);
+        s->mlp.b1 = reinterpret_cast<const float *>(s->mlp_blob + off_b1);
+        s->mlp.b2 = reinterpret_cast<const float *>(s->mlp_blob + off_b2);
+        s->mlp.b3 = reinterpret_cast<const float *>(s->mlp_blob + off_b3);
+        s->has_mlp = true;
+        s->bytes += (int64_t)total;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        dev_free(s->mlp_blob);
+        cudaFree(s->attrs);
+        delete s;
+        return cuda_fail(e, "scene upload");
+    }
+    *out = s;
+    return MGS_OK;
+}
+
+mgs_status mgs_unload_scene(mgs_scene s) {
+    if (!s) return MGS_OK;
+    DeviceGuard g(s->ctx->device);
+    cudaFree(s->attrs);
+    dev_free(s->mlp_blob);
+    delete s;
+    return MGS_OK;
+}
+
+int64_t mgs_scene_bytes(mgs_scene s) { return s ? s->bytes : 0; }
+
+mgs_status mgs_workspace_create(mgs_ctx ctx, mgs_workspace *out) {
+    if (!ctx || !out) return fail(MGS_ERR_INVALID_ARG, "NULL argument");
+    mgs_workspace w = new mgs_workspace_s;
+    w->ctx = ctx;
+    *out = w;
+    return MGS_OK;
+}
+
+mgs_status mgs_workspace_destroy(mgs_workspace w) {
+    if (!w) return MGS_OK;
+    DeviceGuard g(w->ctx->device);
+    dev_free(w->rec);
+    dev_free(w->rect);
+    dev_free(w->tile_count);
+    dev_free(w->tile_offsets);
+    dev_free(w->tile_cursor);
+    dev_free(w->gids);
+    dev_free(w->img);
+    dev_free(w->status);
+    for (auto &q : w->pending)
+        for (auto x : q) cudaEventDestroy(x);
+    for (auto x : w->event_pool) cudaEventDestroy(x);
+    delete w;
+    return MGS_OK;
+}
+
+mgs_status mgs_workspace_reserve(mgs_workspace w, int64_t n, int32_t width, int32_t height,
+                                 int64_t pairs) {
+    if (!w) return fail(MGS_ERR_INVALID_ARG, "workspace is NULL");
+    if (n < 0 || pairs < 0 || width < 1 || height < 1 || width > 16384 || height > 16384)
+        return fail(MGS_ERR_INVALID_ARG, "bad reserve sizes");
+    DeviceGuard g(w->ctx->device);
+    const int64_t T = (int64_t)((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile);
+    return ws_ensure(w, n, T, (uint64_t)pairs);
+}
+
+int64_t mgs_workspace_bytes(mgs_workspace w) { return w ? ws_bytes(w) : 0; }
+
+mgs_status mgs_workspace_sync(mgs_workspace w, mgs_stream stream_, int64_t *pairs_out) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!w) return fail(MGS_ERR_INVALID_ARG, "workspace is NULL");
+    DeviceGuard g(w->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if (pairs_out) *pairs_out = 0;
+    if (!w->status) return MGS_OK;
+    DevStatus h;
+    if ((e = cudaMemcpy(&h, w->status, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    if ((e = cudaMemset(w->status, 0, offsetof(DevStatus, last_pairs))) != cudaSuccess)
+        return cuda_fail(e, "status reset");
+    if (pairs_out) *pairs_out = (int64_t)h.max_pairs;
+    if (h.overflow) {
+        uint64_t need = h.max_pairs + h.max_pairs / 4 + 1024;
+        if (w->grow_hint < need) w->grow_hint = need;
+        return fail(MGS_ERR_OVERFLOW, "tile lists needed %llu pairs, capacity was %llu",
+                    (unsigned long long)h.max_pairs, (unsigned long long)w->pair_cap);
+    }
+    return MGS_OK;
+}
+
+mgs_status mgs_workspace_set_timing(mgs_workspace w, int32_t enable) {
+    if (!w) return fail(MGS_ERR_INVALID_ARG, "workspace is NULL");
+    w->timing = enable != 0;
+    return MGS_OK;
+}
+
+mgs_status mgs_workspace_stage_times(mgs_workspace w, mgs_stream stream_, double ms[3],
+                                     int64_t *frames) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!w || !ms || !frames) return fail(MGS_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard g(w->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    ms[0] = ms[1] = ms[2] = 0.0;
+    *frames = (int64_t)w->pending.size();
+    for (auto &q : w->pending) {
+        for (int k = 0; k < 3; ++k) {
+            float t = 0.f;
+            if ((e = cudaEventElapsedTime(&t, q[k], q[k + 1])) != cudaSuccess)
+                return cuda_fail(e, "event elapsed time");
+            ms[k] += t;
+        }
+        for (auto x : q) w->event_pool.push_back(x);
+    }
+    w->pending.clear();
+    return MGS_OK;
+}
+
+mgs_status mgs_render(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
+                      const mgs_render_opts *opts, float *out_rgb, float *out_aux,
+                      int32_t *out_count, mgs_stream stream) {
+    return render_impl(w, s, cam, opts, out_rgb, out_aux, out_count,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+mgs_status mgs_render_checked(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
+                              const mgs_render_opts *opts, float *out_rgb, float *out_aux,
+                              int32_t *out_count, mgs_stream stream) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        mgs_status st = mgs_render(w, s, cam, opts, out_rgb, out_aux, out_count, stream);
+        if (st != MGS_OK) return st;
+        st = mgs_workspace_sync(w, stream, nullptr);
+        if (st != MGS_ERR_OVERFLOW) return st;
+    }
+    return MGS_ERR_OVERFLOW;
+}
+
+mgs_status mgs_render_to_host(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
+                              const mgs_render_opts *opts, float *host_rgb, mgs_stream stream_) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!w) return fail(MGS_ERR_INVALID_ARG, "workspace is NULL");
+    if (!host_rgb) return fail(MGS_ERR_INVALID_ARG, "host_rgb is NULL");
+    mgs_status st = check_camera(cam);
+    if (st != MGS_OK) return st;
+    DeviceGuard g(w->ctx->device);
+    const int64_t px = (int64_t)cam->width * cam->height;
+    if (px > w->img_cap) {
+        dev_free(w->img);
+        w->img_cap = 0;
+        cudaError_t e = dev_alloc(&w->img, (size_t)px * 3);
+        if (e != cudaSuccess) return cuda_fail(e, "workspace image");
+        w->img_cap = px;
+    }
+    st = render_impl(w, s, cam, opts, w->img, nullptr, nullptr, stream);
+    if (st != MGS_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(host_rgb, w->img, (size_t)px * 12, cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "image copy");
+    return MGS_OK;
+}
+
+mgs_status mgs_tile_lists(mgs_workspace w, mgs_stream stream_, int64_t *n_tiles,
+                          int64_t *n_pairs, uint32_t *offsets_out, uint32_t *gids_out) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!w || !n_tiles || !n_pairs) return fail(MGS_ERR_INVALID_ARG, "NULL argument");
+    *n_tiles = *n_pairs = 0;
+    if (!w->status || w->last_tiles == 0) return fail(MGS_ERR_INVALID_ARG, "no render yet");
+    DeviceGuard g(w->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    DevStatus h;
+    if ((e = cudaMemcpy(&h, w->status, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    *n_tiles = w->last_tiles;
+    *n_pairs = (int64_t)h.last_pairs;
+    if (h.last_pairs > w->pair_cap)
+        return fail(MGS_ERR_OVERFLOW, "the last render overflowed its tile lists");
+    if (offsets_out && gids_out) {
+        e = cudaMemcpy(offsets_out, w->tile_offsets, (size_t)(w->last_tiles + 1) * 4,
+                       cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess && h.last_pairs)
+            e = cudaMemcpy(gids_out, w->gids, (size_t)h.last_pairs * 4, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "tile list copy");
+    }
+    return MGS_OK;
+}
+
+}  // extern "C"

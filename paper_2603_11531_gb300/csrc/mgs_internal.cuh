@@ -1,0 +1,94 @@
+// Internal declarations shared by the CUDA translation units of the renderer.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mobilegs.h"
+
+namespace mgs {
+
+constexpr int kTile = 16;         // tile edge in pixels (binning granularity)
+constexpr int kRec = 24;          // stored elements per Gaussian
+constexpr int kMlpIn = 22;        // [P(3), s(3), q(4), Y(12)]
+constexpr int kMlpK1 = 32;        // layer-1 K padded for the MMA
+constexpr int kMlpHidden = 64;
+constexpr int kMlpOut = 5;        // phi, o, d_r, d_g, d_b
+constexpr int kMlpN3 = 8;         // head N padded for the MMA
+
+// Camera as the kernels see it.
+struct DevCamera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int width, height;
+    float znear;
+    int tiles_x, tiles_y;
+};
+
+// Packed MLP weights in device memory (BF16, row-major [out][in], padded).
+struct DevMLP {
+    const __nv_bfloat16 *w1;  // [64][32]
+    const __nv_bfloat16 *w2;  // [64][64]
+    const __nv_bfloat16 *w3;  // [8][64]
+    const float *b1;          // [64]
+    const float *b2;          // [64]
+    const float *b3;          // [8]
+};
+
+// Device-visible status of a workspace (accumulates until the host syncs).
+struct DevStatus {
+    unsigned int overflow;          // nonzero: some render exceeded capacity
+    unsigned int pad;
+    unsigned long long max_pairs;   // largest pair count seen since the last sync
+    unsigned long long last_pairs;  // pair count of the most recent render
+};
+
+// Projected Gaussian (48 bytes), written by preprocessing, read by the
+// rasteriser:
+//   a = (m_x, m_y, l11, l21)          FP32-contract mean and factors
+//   b = (l22, log2 o, -w, -w c_r)
+//   c = (-w c_g, -w c_b, 0, 0)
+// The inclusion test is q = (l11 dx + l21 dy)^2 + (l22 dy)^2 <= 9 with
+// dx = x + 0.5 - m_x, dy = y + 0.5 - m_y, evaluated exactly as
+// e1 = fma(l11, dx, l21*dy), e2 = l22*dy, q = fma(e1, e1, e2*e2).
+struct __align__(16) ProjRec {
+    float4 a, b, c;
+};
+
+struct RenderArgs {
+    const void *attrs;
+    int64_t n;
+    int precision;
+    int use_mlp;
+    int rgb_residual;
+    DevMLP mlp;
+    DevCamera cam;
+    float bg[3];
+    unsigned flags;
+    // workspace
+    ProjRec *rec;
+    uint2 *rect;              // packed (x_lo | x_hi << 16, y_lo | y_hi << 16)
+    uint32_t *tile_count;     // [T]
+    uint32_t *tile_offsets;   // [T + 1]
+    uint32_t *tile_cursor;    // [T]
+    uint32_t *gids;           // [capacity]
+    uint64_t capacity;
+    DevStatus *status;
+    // outputs
+    float *out_rgb;
+    float *out_aux;
+    int32_t *out_count;
+};
+
+// Launchers (each enqueues its kernels on `stream`).
+// Resets tile_count[0..T) and launches preprocessing.
+cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream,
+                              uint32_t *tile_count, int64_t T);
+cudaError_t launch_binning(const RenderArgs &a, cudaStream_t stream);
+cudaError_t launch_raster(const RenderArgs &a, cudaStream_t stream);
+
+}  // namespace mgs

@@ -1,0 +1,67 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares (no compute calls: CPU only)."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(mgs_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2603_11531_gb300 import build
+    return build.build()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert {"mgs_render", "mgs_load_scene", "mgs_workspace_sync"} <= names
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\b(mgs_\w+)$", out, flags=re.M))
+    missing = _declared() - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+
+
+def test_binding_lists_every_declared_symbol():
+    import paper_2603_11531_gb300 as m
+    assert set(m.EXPORTS) == _declared()
+
+
+def test_library_loads_without_gpu(built):
+    import paper_2603_11531_gb300 as m
+    L = m.lib()
+    for name in m.EXPORTS:
+        assert hasattr(L, name)
+    assert "sm_103a" in m.mgs_version()
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    import paper_2603_11531_gb300 as m
+    monkeypatch.setattr(m, "_lib", None)
+    monkeypatch.setattr(m, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        m.lib()
+
+
+def test_no_cpu_fallback_in_package():
+    """The renderer package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_2603_11531_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
+        src = open(path).read()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), path
