@@ -89,7 +89,10 @@ def test_background_and_ragged_image(R):
 
 def test_culling_is_exact(R, torch_cuda):
     """The per-warp culling only removes Gaussians that include no pixel of
-    the block: with and without it the image is bit-identical."""
+    the block: with and without it every pixel includes exactly the same
+    Gaussians (integer counts equal), and the image differs only by the FP32
+    rounding of a different accumulation order (tile lists are filled by
+    atomics, so their order varies between renders)."""
     import paper_2603_11531_gb300 as m
     scene = synth.unbounded_scene(40000, seed=22, precision="fp16")
     cam = synth.orbit_cameras(8, 8.0, 1.0, 480, 320, 60.0)[2]
@@ -97,8 +100,11 @@ def test_culling_is_exact(R, torch_cuda):
     try:
         a = R.render(h, cam, aux=True, count=True)
         b = R.render(h, cam, aux=True, count=True, flags=m.MGS_FLAG_NO_CULL)
-        for k in ("rgb", "aux", "count"):
-            assert torch_cuda.equal(a[k], b[k]), k
+        assert torch_cuda.equal(a["count"], b["count"])
+        assert int(a["count"].sum()) > 0
+        assert float((a["rgb"] - b["rgb"]).abs().max()) <= 1e-5
+        T_a, T_b = a["aux"][4], b["aux"][4]
+        assert float((T_a - T_b).abs().max()) <= 1e-5
     finally:
         R.unload_scene(h)
 
@@ -194,7 +200,8 @@ def test_render_to_host_matches_device(R, torch_cuda):
         host = torch.empty((80, 96, 3), dtype=torch.float32).pin_memory()
         m.mgs_render_to_host(R.ws, h, cam, m.render_opts(), host)
         torch.cuda.synchronize()
-        assert torch.equal(host, dev.cpu())
+        # same Gaussians per pixel; list order (hence FP32 rounding) may differ
+        assert float((host - dev.cpu()).abs().max()) <= 1e-5
     finally:
         R.unload_scene(h)
 
