@@ -90,8 +90,9 @@ struct mgs_workspace_s {
     uint2 *rect = nullptr;
     uint32_t *tile_count = nullptr;
     uint32_t *tile_offsets = nullptr;
-    uint32_t *tile_cursor = nullptr;
     uint32_t *gids = nullptr;
+    uint32_t *bases = nullptr;   // [binning CTAs][tiles] block bases
+    int64_t bases_cap = 0;
     float *img = nullptr;
     DevStatus *status = nullptr;
     int64_t last_tiles = 0;
@@ -105,8 +106,8 @@ namespace {
 
 int64_t ws_bytes(const mgs_workspace_s *w) {
     return w->n_cap * (int64_t)(sizeof(ProjRec) + sizeof(uint2)) +
-           w->tiles_cap * 3 * (int64_t)sizeof(uint32_t) + (int64_t)w->pair_cap * 4 +
-           w->img_cap * 12 + (int64_t)sizeof(DevStatus);
+           w->tiles_cap * 2 * (int64_t)sizeof(uint32_t) + (int64_t)w->pair_cap * 4 +
+           w->img_cap * 12 + w->bases_cap * 4 + (int64_t)sizeof(DevStatus);
 }
 
 mgs_status ws_ensure(mgs_workspace_s *w, int64_t n, int64_t tiles, uint64_t pairs) {
@@ -122,12 +123,10 @@ mgs_status ws_ensure(mgs_workspace_s *w, int64_t n, int64_t tiles, uint64_t pair
     if (tiles + 1 > w->tiles_cap) {
         dev_free(w->tile_count);
         dev_free(w->tile_offsets);
-        dev_free(w->tile_cursor);
         w->tiles_cap = 0;
         const size_t t = (size_t)tiles + 1;
         if ((e = dev_alloc(&w->tile_count, t)) != cudaSuccess) return cuda_fail(e, "workspace");
         if ((e = dev_alloc(&w->tile_offsets, t)) != cudaSuccess) return cuda_fail(e, "workspace");
-        if ((e = dev_alloc(&w->tile_cursor, t)) != cudaSuccess) return cuda_fail(e, "workspace");
         w->tiles_cap = (int64_t)t;
     }
     if (pairs > w->pair_cap) {
@@ -136,6 +135,13 @@ mgs_status ws_ensure(mgs_workspace_s *w, int64_t n, int64_t tiles, uint64_t pair
         w->pair_cap = 0;
         if ((e = dev_alloc(&w->gids, (size_t)pairs)) != cudaSuccess) return cuda_fail(e, "workspace");
         w->pair_cap = pairs;
+    }
+    const int64_t nb = (int64_t)bin_ctas(n, w->ctx->sm_count) * tiles;
+    if (nb > w->bases_cap) {
+        dev_free(w->bases);
+        w->bases_cap = 0;
+        if ((e = dev_alloc(&w->bases, (size_t)nb)) != cudaSuccess) return cuda_fail(e, "workspace");
+        w->bases_cap = nb;
     }
     if (!w->status) {
         if ((e = dev_alloc(&w->status, 1)) != cudaSuccess) return cuda_fail(e, "workspace");
@@ -220,7 +226,6 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     a.rect = w->rect;
     a.tile_count = w->tile_count;
     a.tile_offsets = w->tile_offsets;
-    a.tile_cursor = w->tile_cursor;
     a.gids = w->gids;
     a.capacity = w->pair_cap;
     a.status = w->status;
@@ -241,12 +246,11 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
         }
         cudaEventRecord(ev[0], stream);
     }
-    if (s->n > 0 && (e = launch_preprocess(a, w->ctx->sm_count, stream, w->tile_count, T)) != cudaSuccess)
+    if (s->n > 0 && (e = launch_preprocess(a, w->ctx->sm_count, stream)) != cudaSuccess)
         return cuda_fail(e, "preprocess launch");
-    if (s->n == 0 && (e = cudaMemsetAsync(w->tile_count, 0, (size_t)T * 4, stream)) != cudaSuccess)
-        return cuda_fail(e, "memset");
     if (w->timing) cudaEventRecord(ev[1], stream);
-    if ((e = launch_binning(a, stream)) != cudaSuccess) return cuda_fail(e, "binning launch");
+    if ((e = launch_binning(a, w->ctx->sm_count, w->bases, stream)) != cudaSuccess)
+        return cuda_fail(e, "binning launch");
     if (w->timing) cudaEventRecord(ev[2], stream);
     if ((e = launch_raster(a, stream)) != cudaSuccess) return cuda_fail(e, "raster launch");
     if (w->timing) {
@@ -405,8 +409,8 @@ mgs_status mgs_workspace_destroy(mgs_workspace w) {
     dev_free(w->rect);
     dev_free(w->tile_count);
     dev_free(w->tile_offsets);
-    dev_free(w->tile_cursor);
     dev_free(w->gids);
+    dev_free(w->bases);
     dev_free(w->img);
     dev_free(w->status);
     for (auto &q : w->pending)

@@ -2,22 +2,142 @@
 //
 // The paper removes depth sorting because the blending sums of Eq. 2 commute
 // (Sec. 2, Eq. 1 discussion; Sec. 3.1).  The lists built here are keyed by
-// tile only: per-tile counts (accumulated by preprocessing) -> exclusive scan
-// -> scatter of each Gaussian index into every tile of its rectangle.  A
-// tile's list order is whatever order the scatter produced; the rasteriser
-// does not depend on it beyond FP32 rounding.
+// tile only -- a counting sort by tile:
+//
+//   1. k_bin_count: CTA c owns a contiguous range of Gaussians and counts its
+//      (tile, Gaussian) pairs into a shared-memory histogram over the tiles;
+//      one global atomicAdd per (CTA, tile) reserves the CTA's block inside
+//      the tile and returns its base.
+//   2. k_scan: exclusive scan of the per-tile totals -> tile offsets.
+//   3. k_bin_scatter: the same CTA re-expands its pairs and places each one at
+//      offset[tile] + base[c][tile] + (shared-memory rank).
+//
+// Pairs are expanded warp-cooperatively: a warp's 32 Gaussians are flattened
+// into one pair index space (prefix sum of rectangle areas) so a Gaussian
+// covering thousands of tiles does not serialise one lane.  Order within a
+// tile follows the atomics and is not reproducible; the rasteriser does not
+// depend on it beyond FP32 rounding.
 #include "mgs_internal.cuh"
 
 namespace mgs {
 namespace {
 
 constexpr int kScanThreads = 1024;
+constexpr int kBinThreads = 1024;
+constexpr int kBand = 32768;          // tiles per shared-memory band (128 KB)
 
-// Exclusive scan of tile_count[T] into tile_offsets[T+1] and tile_cursor[T],
-// by one block.  Also records the pair count and flags capacity overflow.
+__device__ __forceinline__ void rect_of(const uint2 r, int &x0, int &y0, int &w, int &h) {
+    x0 = r.x & 0xFFFF;
+    y0 = r.y & 0xFFFF;
+    w = (int)(r.x >> 16) - x0;
+    h = (int)(r.y >> 16) - y0;
+}
+
+// Calls f(tile, gid) for every (tile, Gaussian) pair of Gaussians
+// [g0, g0 + 32) (one per lane), spreading the pairs over the warp's lanes.
+template <class F>
+__device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect, int64_t n, int64_t g0,
+                                           int tiles_x, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = g0 + lane;
+    int x0 = 0, y0 = 0, w = 0, h = 0;
+    if (i < n) rect_of(rect[i], x0, y0, w, h);
+    const int c = w * h;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int excl = incl - c;
+    const int P = __shfl_sync(0xffffffffu, incl, 31);
+    for (int pb = 0; pb < P; pb += 32) {
+        const int p = pb + lane;
+        // owner: the largest lane whose exclusive prefix is <= p
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(0xffffffffu, excl, lo + step);
+            if (e <= p) lo += step;
+        }
+        const int ox0 = __shfl_sync(0xffffffffu, x0, lo);
+        const int oy0 = __shfl_sync(0xffffffffu, y0, lo);
+        const int ow = __shfl_sync(0xffffffffu, w, lo);
+        const int oe = __shfl_sync(0xffffffffu, excl, lo);
+        if (p < P) {
+            const int k = p - oe;
+            const int ky = k / ow;
+            const int tile = (oy0 + ky) * tiles_x + ox0 + (k - ky * ow);
+            f(tile, (uint32_t)(g0 + lo));
+        }
+    }
+}
+
+__device__ __forceinline__ void cta_range(int64_t n, int64_t &begin, int64_t &end) {
+    const int64_t per = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+    begin = per * blockIdx.x;
+    end = begin + per < n ? begin + per : n;
+}
+
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(const uint2 *__restrict__ rect,
+                                                           int64_t n, int tiles_x, int T,
+                                                           uint32_t *__restrict__ tile_count,
+                                                           uint32_t *__restrict__ bases) {
+    extern __shared__ uint32_t cnt_s[];
+    int64_t begin, end;
+    cta_range(n, begin, end);
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int band0 = 0; band0 < T; band0 += kBand) {
+        const int bn = min(kBand, T - band0);
+        for (int t = threadIdx.x; t < bn; t += blockDim.x) cnt_s[t] = 0u;
+        __syncthreads();
+        for (int64_t g0 = begin + 32 * warp; g0 < end; g0 += 32 * nwarps) {
+            warp_pairs(rect, end, g0, tiles_x, [&](int tile, uint32_t) {
+                const int t = tile - band0;
+                if ((unsigned)t < (unsigned)bn) atomicAdd(&cnt_s[t], 1u);
+            });
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < bn; t += blockDim.x) {
+            const uint32_t v = cnt_s[t];
+            if (v) bases[(int64_t)blockIdx.x * T + band0 + t] = atomicAdd(&tile_count[band0 + t], v);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(
+    const uint2 *__restrict__ rect, int64_t n, int tiles_x, int T,
+    const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ bases,
+    uint32_t *__restrict__ gids, uint64_t capacity, const DevStatus *__restrict__ status) {
+    extern __shared__ uint32_t cur_s[];
+    if (status->last_pairs > capacity) return;  // overflow: lists are not built
+    int64_t begin, end;
+    cta_range(n, begin, end);
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int band0 = 0; band0 < T; band0 += kBand) {
+        const int bn = min(kBand, T - band0);
+        // entries of tiles this CTA has no pairs in are never read
+        for (int t = threadIdx.x; t < bn; t += blockDim.x)
+            cur_s[t] = offsets[band0 + t] + bases[(int64_t)blockIdx.x * T + band0 + t];
+        __syncthreads();
+        for (int64_t g0 = begin + 32 * warp; g0 < end; g0 += 32 * nwarps) {
+            warp_pairs(rect, end, g0, tiles_x, [&](int tile, uint32_t gid) {
+                const int t = tile - band0;
+                if ((unsigned)t < (unsigned)bn) {
+                    const uint32_t slot = atomicAdd(&cur_s[t], 1u);
+                    if (slot < capacity) gids[slot] = gid;
+                }
+            });
+        }
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of tile_count[T] into tile_offsets[T+1], by one block; also
+// records the pair count and flags capacity overflow.
 __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restrict__ count,
-                                                       uint32_t *__restrict__ offsets,
-                                                       uint32_t *__restrict__ cursor, int T,
+                                                       uint32_t *__restrict__ offsets, int T,
                                                        uint64_t capacity, DevStatus *status) {
     __shared__ unsigned long long warp_sums[kScanThreads / 32];
     __shared__ unsigned long long carry;
@@ -25,7 +145,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
     if (tid == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < T; base += kScanThreads * 4) {
-        // each thread owns 4 consecutive tiles of this chunk
         const int i0 = base + tid * 4;
         unsigned long long v[4], local = 0;
 #pragma unroll
@@ -48,16 +167,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
                 unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
                 if (lane >= o) s += y;
             }
-            warp_sums[lane] = s;  // inclusive over warps
+            warp_sums[lane] = s;
         }
         __syncthreads();
         unsigned long long run = carry + (incl - local) + (warp > 0 ? warp_sums[warp - 1] : 0ull);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (i0 + k < T) {
-                offsets[i0 + k] = (uint32_t)run;
-                cursor[i0 + k] = (uint32_t)run;
-            }
+            if (i0 + k < T) offsets[i0 + k] = (uint32_t)run;
             run += v[k];
         }
         __syncthreads();
@@ -73,34 +189,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
     }
 }
 
-// Scatter: Gaussian i is appended to every tile of its rectangle.
-__global__ void __launch_bounds__(256) k_scatter(const uint2 *__restrict__ rect, int64_t n,
-                                                 int tiles_x, uint32_t *__restrict__ cursor,
-                                                 uint32_t *__restrict__ gids, uint64_t capacity,
-                                                 const DevStatus *__restrict__ status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (status->last_pairs > capacity) return;
-    const uint2 r = rect[i];
-    const int x0 = r.x & 0xFFFF, x1 = r.x >> 16, y0 = r.y & 0xFFFF, y1 = r.y >> 16;
-    for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) {
-            const uint32_t slot = atomicAdd(&cursor[ty * tiles_x + tx], 1u);
-            if (slot < capacity) gids[slot] = (uint32_t)i;
-        }
-}
-
 }  // namespace
 
-cudaError_t launch_binning(const RenderArgs &a, cudaStream_t stream) {
+int bin_ctas(int64_t n, int sm_count) {
+    int64_t c = (n + kBinThreads - 1) / kBinThreads;
+    const int64_t cap = 2 * (int64_t)sm_count;
+    if (c > cap) c = cap;
+    return c < 1 ? 1 : (int)c;
+}
+
+cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases,
+                           cudaStream_t stream) {
     const int T = a.cam.tiles_x * a.cam.tiles_y;
-    k_scan<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, a.tile_cursor, T,
-                                           a.capacity, a.status);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || a.n == 0) return e;
-    const int64_t blocks = (a.n + 255) / 256;
-    k_scatter<<<(unsigned)blocks, 256, 0, stream>>>(a.rect, a.n, a.cam.tiles_x, a.tile_cursor,
-                                                    a.gids, a.capacity, a.status);
+    const int C = bin_ctas(a.n, sm_count);
+    const size_t smem = (size_t)(T < kBand ? T : kBand) * sizeof(uint32_t);
+    cudaError_t e = cudaMemsetAsync(a.tile_count, 0, (size_t)T * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    if (a.n > 0) {
+        if ((e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kBand * sizeof(uint32_t)))) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kBand * sizeof(uint32_t)))) != cudaSuccess)
+            return e;
+        k_bin_count<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, a.tile_count,
+                                                      bases);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_scan<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, T, a.capacity, a.status);
+    if ((e = cudaGetLastError()) != cudaSuccess || a.n == 0) return e;
+    k_bin_scatter<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, a.tile_offsets,
+                                                    bases, a.gids, a.capacity, a.status);
     return cudaGetLastError();
 }
 

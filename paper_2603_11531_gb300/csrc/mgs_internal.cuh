@@ -74,7 +74,6 @@ struct RenderArgs {
     uint2 *rect;              // packed (x_lo | x_hi << 16, y_lo | y_hi << 16)
     uint32_t *tile_count;     // [T]
     uint32_t *tile_offsets;   // [T + 1]
-    uint32_t *tile_cursor;    // [T]
     uint32_t *gids;           // [capacity]
     uint64_t capacity;
     DevStatus *status;
@@ -85,10 +84,10 @@ struct RenderArgs {
 };
 
 // Launchers (each enqueues its kernels on `stream`).
-// Resets tile_count[0..T) and launches preprocessing.
-cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream,
-                              uint32_t *tile_count, int64_t T);
-cudaError_t launch_binning(const RenderArgs &a, cudaStream_t stream);
+cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream);
+// Per-tile counts, scan and scatter.  `bases` has bin_ctas(...) * T entries.
+cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases, cudaStream_t stream);
+int bin_ctas(int64_t n, int sm_count);
 cudaError_t launch_raster(const RenderArgs &a, cudaStream_t stream);
 
 }  // namespace mgs

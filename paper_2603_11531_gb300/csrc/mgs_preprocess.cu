@@ -5,7 +5,7 @@
 //   Sec. 3.2 first-order SH colour,
 //   Eq. 4    enhancement MLP (BF16 tensor cores, FP32 accumulation),
 //   Eq. 3    depth-aware weight w_i,
-// plus the tile rectangle and per-tile counts used by binning.
+// plus the tile rectangle used by binning.
 //
 // Visibility, the tile rectangle and the inclusion-test factors follow a fixed
 // sequence of correctly rounded FP32 operations (no contraction, explicit
@@ -406,9 +406,6 @@ __global__ void __launch_bounds__(kThreads)
         args.rec[i] = r;
         args.rect[i] = make_uint2((unsigned)c.rect[0] | ((unsigned)c.rect[2] << 16),
                                   (unsigned)c.rect[1] | ((unsigned)c.rect[3] << 16));
-        for (int ty = c.rect[1]; ty < c.rect[3]; ++ty)
-            for (int tx = c.rect[0]; tx < c.rect[2]; ++tx)
-                atomicAdd(&args.tile_count[ty * cam.tiles_x + tx], 1u);
     }
 }
 
@@ -431,10 +428,7 @@ cudaError_t launch_t(const RenderArgs &a, int sm_count, cudaStream_t stream) {
 
 }  // namespace
 
-cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream,
-                              uint32_t *tile_count, int64_t T) {
-    cudaError_t e = cudaMemsetAsync(tile_count, 0, (size_t)T * sizeof(uint32_t), stream);
-    if (e != cudaSuccess) return e;
+cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream) {
     const bool fp16 = a.precision == MGS_PREC_FP16;
     if (a.use_mlp) {
         if (a.rgb_residual)

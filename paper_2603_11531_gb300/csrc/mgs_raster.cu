@@ -4,12 +4,11 @@
 //   C = (1 - T) A / B + T c_bg          (foreground term 0 when B = 0)
 //
 // One CTA per 16x16 tile, 128 threads, each thread owning two horizontally
-// adjacent pixels (packed FP32x2 arithmetic).  The tile's Gaussian list is
-// walked in batches of 128: each thread stages one projected Gaussian into
-// shared memory and tests it against the four 16x4-pixel warp blocks with a
-// conservative bound; each warp then compacts (ballot) the Gaussians that can
-// touch its block and accumulates them in registers.  No atomics, no sort:
-// every pixel is owned by exactly one thread.
+// adjacent pixels (packed FP32x2 arithmetic).  Each warp owns an 8x8 block and
+// walks the tile's Gaussian list itself, testing each entry against its block
+// with a conservative bound and compacting (ballot) the candidates before
+// accumulating them in registers.  No atomics, no sort: every pixel is owned
+// by exactly one thread.
 #include "mgs_internal.cuh"
 
 namespace mgs {
@@ -54,11 +53,6 @@ __device__ __forceinline__ float ex2(float x) {
 //   s0 = {m_x, m_x, m_y, m_y}      s1 = {l11, l11, l21, l21}
 //   s2 = {l22, l22, log2 o, log2 o} s3 = {-w, -w, -w c_r, -w c_r}
 //   s4 = {-w c_g, -w c_g, -w c_b, -w c_b}
-struct Stage {
-    ulonglong2 s[5][kThreads];
-    unsigned char mask[kThreads];
-    unsigned char list[kWarps][kThreads];
-};
 
 // Can Gaussian (m, l) include any pixel centre of the block centred at (bx, by)
 // with half extents (hx, hy)?  Sound for the exact FP32 test: the slab bounds
@@ -77,21 +71,29 @@ __device__ __forceinline__ bool block_may_hit(float mx, float my, float l11, flo
     return (e1c - h1 <= 3.0f + m1) && (e2c - h2 <= 3.0f + m2);
 }
 
+// One CTA per tile; warp w owns the 8x8 pixel block (w & 1, w >> 1) of the
+// tile, lane l the pixel pair (2 (l & 3), l >> 2) of that block.  Each warp
+// streams the tile's list on its own (no block-wide barrier): 32 entries at a
+// time, one per lane, are fetched, tested against the warp's block, and the
+// candidates are compacted into the warp's shared-memory buffer and then
+// accumulated by all lanes.
 template <bool kAux, bool kCount>
 __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
-    __shared__ Stage st;
+    __shared__ ulonglong2 buf[kWarps][5][32];
     const DevCamera &cam = args.cam;
     const int tile = blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int px = tx * kTile + 2 * (lane & 7);
-    const int py = ty * kTile + 4 * warp + (lane >> 3);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx0 = tx * kTile + 8 * (warp & 1), by0 = ty * kTile + 8 * (warp >> 1);
+    const int px = bx0 + 2 * (lane & 3);
+    const int py = by0 + (lane >> 2);
 
     if (args.status->last_pairs > args.capacity) return;  // overflowed: lists incomplete
 
     const uint32_t start = args.tile_offsets[tile];
     const uint32_t end = args.tile_offsets[tile + 1];
     const bool no_cull = (args.flags & MGS_FLAG_NO_CULL) != 0;
+    const float bx = (float)bx0 + 4.0f, by = (float)by0 + 4.0f;
 
     const f2 pxc = pk((float)px + 0.5f, (float)px + 1.5f);
     const f2 pyc = pk((float)py + 0.5f, (float)py + 0.5f);
@@ -100,49 +102,33 @@ __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
     f2 Ar = 0ull, Ag = 0ull, Ab = 0ull, B = 0ull;
     f2 T = pk(1.0f, 1.0f);
     int cnt0 = 0, cnt1 = 0;
+    ulonglong2(*wb)[32] = buf[warp];
 
-    const float bx = (float)(tx * kTile) + 8.0f;
-
-    for (uint32_t base = start; base < end; base += kThreads) {
-        const uint32_t j = base + tid;
-        unsigned m = 0;
+    for (uint32_t base = start; base < end; base += 32) {
+        const uint32_t j = base + lane;
+        bool cand = false;
+        float4 a, b, c;
         if (j < end) {
-            const uint32_t gid = args.gids[j];
-            const float4 a = __ldg(&args.rec[gid].a);
-            const float4 b = __ldg(&args.rec[gid].b);
-            const float4 c = __ldg(&args.rec[gid].c);
-            st.s[0][tid] = make_ulonglong2(pk(a.x, a.x), pk(a.y, a.y));
-            st.s[1][tid] = make_ulonglong2(pk(a.z, a.z), pk(a.w, a.w));
-            st.s[2][tid] = make_ulonglong2(pk(b.x, b.x), pk(b.y, b.y));
-            st.s[3][tid] = make_ulonglong2(pk(b.z, b.z), pk(b.w, b.w));
-            st.s[4][tid] = make_ulonglong2(pk(c.x, c.x), pk(c.y, c.y));
-            if (no_cull) {
-                m = (1u << kWarps) - 1u;
-            } else {
-#pragma unroll
-                for (int w = 0; w < kWarps; ++w) {
-                    const float by = (float)(ty * kTile + 4 * w) + 2.0f;
-                    if (block_may_hit(a.x, a.y, a.z, a.w, b.x, bx, by, 7.5f, 1.5f)) m |= 1u << w;
-                }
-            }
+            const uint32_t gid = __ldg(&args.gids[j]);
+            a = __ldg(&args.rec[gid].a);
+            b = __ldg(&args.rec[gid].b);
+            c = __ldg(&args.rec[gid].c);
+            cand = no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bx, by, 3.5f, 3.5f);
         }
-        st.mask[tid] = (unsigned char)m;
-        __syncthreads();
-        // compact this warp's candidates
-        int nw = 0;
-#pragma unroll
-        for (int c = 0; c < kWarps; ++c) {
-            const int idx = c * 32 + lane;
-            const bool hit = (st.mask[idx] >> warp) & 1u;
-            const unsigned bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) st.list[warp][nw + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)idx;
-            nw += __popc(bal);
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (cand) {
+            const int pos = __popc(bal & ((1u << lane) - 1u));
+            wb[0][pos] = make_ulonglong2(pk(a.x, a.x), pk(a.y, a.y));
+            wb[1][pos] = make_ulonglong2(pk(a.z, a.z), pk(a.w, a.w));
+            wb[2][pos] = make_ulonglong2(pk(b.x, b.x), pk(b.y, b.y));
+            wb[3][pos] = make_ulonglong2(pk(b.z, b.z), pk(b.w, b.w));
+            wb[4][pos] = make_ulonglong2(pk(c.x, c.x), pk(c.y, c.y));
         }
         __syncwarp();
+        const int n = __popc(bal);
 #pragma unroll 2
-        for (int k = 0; k < nw; ++k) {
-            const int g = st.list[warp][k];
-            const ulonglong2 s0 = st.s[0][g], s1 = st.s[1][g], s2 = st.s[2][g];
+        for (int k = 0; k < n; ++k) {
+            const ulonglong2 s0 = wb[0][k], s1 = wb[1][k], s2 = wb[2][k];
             // inclusion test (exact FP32 sequence)
             const f2 dx = sub2(pxc, s0.x);
             const f2 dy = sub2(pyc, s0.y);
@@ -163,14 +149,14 @@ __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
                 cnt1 += q1 <= 9.0f;
             }
             const f2 na = pk(n0, n1);
-            const ulonglong2 s3 = st.s[3][g], s4 = st.s[4][g];
+            const ulonglong2 s3 = wb[3][k], s4 = wb[4][k];
             Ar = fma2(na, s3.y, Ar);
             Ag = fma2(na, s4.x, Ag);
             Ab = fma2(na, s4.y, Ab);
             B = fma2(na, s3.x, B);
             T = fma2(na, T, T);
         }
-        __syncthreads();
+        __syncwarp();
     }
 
     if (py >= cam.height) return;
