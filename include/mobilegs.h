@@ -196,6 +196,31 @@ mgs_status mgs_tile_lists(mgs_workspace ws, mgs_stream stream, int64_t *n_tiles,
                           int64_t *n_pairs, uint32_t *offsets_out,
                           uint32_t *gids_out);
 
+/* ---- allocation-free rendering -------------------------------------------- */
+
+/* Renders one view without allocating any device memory, for callers that
+ * cannot call cudaMalloc (code where the device allocator is forbidden or
+ * unavailable, or a real-time loop that must not take its locks or fail on an
+ * out-of-memory condition).  The paper has no counterpart: this is a
+ * deployment variant of mgs_render.
+ *   attrs:     device pointer, n x 24 records (same layout as mgs_scene_desc),
+ *              16-byte aligned; precision MGS_PREC_FP32 or MGS_PREC_FP16.
+ *   out_rgb:   device, height x width x 3 FP32, caller-owned.
+ *   opts:      use_mlp must be 0 (plain mode: phi = 1, stored opacity).
+ * Scratch lives in one fixed __device__ array (about 27 MiB) that every GPU
+ * loading this library holds until the process exits.  Limits: n <= 131072,
+ * at most 8192 tiles of 16x16 pixels (1920x1080 fits), at most 4,194,304
+ * (tile, Gaussian) pairs; larger n or images are rejected with
+ * MGS_ERR_INVALID_ARG before any work, too many pairs with MGS_ERR_OVERFLOW
+ * (the image is then invalid).  The call waits for `stream` before returning.
+ * The first call on a device resolves the array's device address (set-up with
+ * that device current); make it before any stream capture.  All calls share
+ * the array, so calls whose GPU work overlaps race: order them on one stream
+ * or serialise them. */
+mgs_status mgs_render_static(const void *attrs, int64_t n, int32_t precision,
+                             const mgs_camera *cam, const mgs_render_opts *opts,
+                             float *out_rgb, mgs_stream stream);
+
 /* ---- diagnostics --------------------------------------------------------- */
 
 const char *mgs_last_error(void);

@@ -38,6 +38,7 @@ EXPORTS = (
     "mgs_workspace_reserve", "mgs_workspace_bytes", "mgs_workspace_sync", "mgs_render",
     "mgs_render_checked", "mgs_render_to_host", "mgs_tile_lists", "mgs_last_error",
     "mgs_version", "mgs_workspace_set_timing", "mgs_workspace_stage_times",
+    "mgs_render_static",
 )
 
 
@@ -100,6 +101,8 @@ def lib():
                 "mgs_tile_lists": ([P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P], I32),
                 "mgs_workspace_set_timing": ([P, I32], I32),
                 "mgs_workspace_stage_times": ([P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], I32),
+                "mgs_render_static": ([P, I64, I32, ctypes.POINTER(mgs_camera),
+                                       ctypes.POINTER(mgs_render_opts), P, P], I32),
                 "mgs_last_error": ([], ctypes.c_char_p),
                 "mgs_version": ([], ctypes.c_char_p),
             }
@@ -281,6 +284,21 @@ def mgs_workspace_stage_times(ws, stream=None):
     fr = ctypes.c_int64()
     _check(lib().mgs_workspace_stage_times(ws, _stream(stream), ms, ctypes.byref(fr)))
     return [ms[0], ms[1], ms[2]], fr.value
+
+
+def mgs_render_static(attrs, cam, opts, out_rgb, stream=None):
+    """Allocation-free render (see include/mobilegs.h): attrs is a CUDA tensor
+    (N, 24) float32/float16; waits for the stream before returning."""
+    import torch
+    if not (hasattr(attrs, "is_cuda") and attrs.is_cuda):
+        raise TypeError("attrs must be a CUDA tensor")
+    if attrs.dtype not in (torch.float16, torch.float32) or attrs.ndim != 2 or attrs.shape[1] != 24:
+        raise ValueError("attrs must be (N, 24) float16/float32")
+    a = attrs.contiguous()
+    prec = MGS_PREC_FP16 if a.dtype == torch.float16 else MGS_PREC_FP32
+    c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    _check(lib().mgs_render_static(_ptr(a), int(a.shape[0]), prec, ctypes.byref(c),
+                                   ctypes.byref(opts), _ptr(out_rgb), _stream(stream)))
 
 
 def mgs_version() -> str:

@@ -263,6 +263,8 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
 
 }  // namespace
 
+void mgs::set_last_error(const char *msg) { g_err = msg; }
+
 extern "C" {
 
 const char *mgs_last_error(void) { return g_err.c_str(); }

@@ -88,6 +88,8 @@ cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t st
 // Per-tile counts, scan and scatter.  `bases` has bin_ctas(...) * T entries.
 cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases, cudaStream_t stream);
 int bin_ctas(int64_t n, int sm_count);
+// Sets the calling thread's message returned by mgs_last_error().
+void set_last_error(const char *msg);
 cudaError_t launch_raster(const RenderArgs &a, cudaStream_t stream);
 
 }  // namespace mgs
