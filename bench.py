@@ -95,6 +95,21 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+def _profiled_traffic(name):
+    """dram read+write bytes per launch from a committed ncu summary (line
+    'traffic_bytes_per_launch: N'), or None."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.strip().startswith("traffic_bytes_per_launch:"):
+            try:
+                return int(line.split(":", 1)[1].strip())
+            except ValueError:
+                return None
+    return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -102,7 +117,7 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline_sample(tile_stride: int = 32, pose: int = 0):
+def cpu_baseline_sample(tile_stride: int = 8, pose: int = 0):
     """Time the FP64 oracle as it stands (single thread) on one pose of the
     workload: full preprocessing (600k Gaussians incl. MLP) and binning, and
     rasterisation of every `tile_stride`-th tile, scaled to the whole frame."""
@@ -188,11 +203,11 @@ def run_gpu(args):
     # Size the workspace on every pose (checked renders), and count the
     # included (pixel, Gaussian) pairs per pose for the roofline.
     cnt = torch.empty((H, W), dtype=torch.int32, device="cuda")
-    hits = []
+    hits, pairs = [], []
     for c in cstructs:
         m.mgs_render_checked(r.ws, h, c, opts, out, None, cnt, stream)
         hits.append(int(cnt.sum(dtype=torch.int64)))
-    _, pairs = m.mgs_workspace_sync(r.ws, stream)
+        pairs.append(m.mgs_tile_lists(r.ws, stream=stream)[1])
 
     def sweep():
         for c in cstructs:
@@ -264,10 +279,7 @@ def run_gpu(args):
     # (7 for the quadratic form, 9 for alpha and the A/B/T updates) + 1 MUFU
     achieved = 16.0 * mean_hits / (rast["ms_per_frame"] / 1000.0) / 1e12
     peak_alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "raster_traffic.json")
-    if os.path.exists(prof):
-        traffic = json.load(open(prof)).get("bytes_per_launch")
+    traffic = _profiled_traffic("k_raster_unbounded600k_1600x1063.md")
 
     if rank == 0:
         line = {
@@ -279,7 +291,8 @@ def run_gpu(args):
                        "gaussians": scene.n, "resolution": [W, H], "poses_per_step": N_POSES,
                        "attrs": "fp16", "mlp": "bf16 22-64-64-5", "parallelism": "replicas",
                        "l2": "flushed (512 MB write) between timed steps",
-                       "pairs_per_frame_max": pairs, "hits_per_frame_mean": mean_hits},
+                       "pairs_per_frame_mean": sum(pairs) / len(pairs),
+                       "hits_per_frame_mean": mean_hits},
             "e2e": {"value": e2e_fps, "unit": "FPS",
                     "h2d_bytes_per_step": N_POSES * 68,
                     "d2h_bytes_per_step": N_POSES * H * W * 12},
@@ -292,7 +305,7 @@ def run_gpu(args):
                          "stage_ms_per_frame": {"preprocess_mlp": stage_per_frame[0],
                                                 "binning": stage_per_frame[1],
                                                 "raster": stage_per_frame[2]}},
-            "gpu_launches": 4 * N_POSES * args.steps,
+            "gpu_launches": 6 * N_POSES * args.steps,
             "clocks": clocks,
             "peaks": peaks_kind,
         }

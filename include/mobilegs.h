@@ -196,6 +196,29 @@ mgs_status mgs_tile_lists(mgs_workspace ws, mgs_stream stream, int64_t *n_tiles,
                           int64_t *n_pairs, uint32_t *offsets_out,
                           uint32_t *gids_out);
 
+/* ---- differentiation (adjoint of Sec. 3.1 Eq. 2-4, Sec. 3.2, App. B) ------- */
+
+/* Gradients of a loss L with respect to every stored Gaussian attribute and
+ * the MLP parameters, given dL/dC of a render of the same view.
+ *   dL_drgb: device, height x width x 3 FP32 (dL/dC).
+ *   aux:     device, 5 x height x width FP32, the out_aux of mgs_render for
+ *            this scene, camera and options (A_rgb, B, T).
+ *   d_attrs: device, n x 24 FP32, overwritten with dL/d(record element) (the
+ *            widened FP16 values for FP16 scenes; padding 0; the opacity
+ *            column is 0 in MLP mode, where Eq. 4 replaces the stored opacity).
+ *   d_mlp:   device, 5957 FP32 or NULL, overwritten with dL/dW1 [64][22],
+ *            dL/db1 [64], dL/dW2 [64][64], dL/db2 [64], dL/dW3 [5][64],
+ *            dL/db3 [5] (zeros without the MLP).  The BF16 rounding of the
+ *            MLP's tensor-core inputs is passed straight through.
+ * The inclusion test and tile rectangles are piecewise constant; their
+ * derivative is taken as zero.  Asynchronous on `stream`; reuses the
+ * workspace (it rebuilds the frame's records and tile lists). */
+mgs_status mgs_render_backward(mgs_workspace ws, mgs_scene scene,
+                               const mgs_camera *cam,
+                               const mgs_render_opts *opts,
+                               const float *dL_drgb, const float *aux,
+                               float *d_attrs, float *d_mlp, mgs_stream stream);
+
 /* ---- allocation-free rendering -------------------------------------------- */
 
 /* Renders one view without allocating any device memory, for callers that

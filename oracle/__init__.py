@@ -86,6 +86,8 @@ def lib():
             L.orc_rasterize.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int,
                                         ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                         P, P, P]
+            L.orc_pairs.restype = ctypes.c_int64
+            L.orc_pairs.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int64]
             if L.orc_gauss_size() != GAUSS_DTYPE.itemsize:
                 raise RuntimeError("orc_gauss layout mismatch")
             _lib = L
@@ -206,3 +208,16 @@ def mlp_eval(mlp, x) -> np.ndarray:
 def includes(g_row: np.ndarray, px: int, py: int) -> bool:
     one = np.ascontiguousarray(np.asarray(g_row).reshape(1))
     return bool(lib().orc_includes(_ptr(one), int(px), int(py)))
+
+
+def included_pairs(g: np.ndarray, offsets, gids, width: int, height: int):
+    """(pixel_index, gaussian_index) of every included pair (FP32 contract)."""
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    gids = np.ascontiguousarray(gids, np.int32)
+    gp = _ptr(gids if len(gids) else np.zeros(1, np.int32))
+    n = lib().orc_pairs(_ptr(g), _ptr(offsets), gp, width, height, None, None, 0)
+    pix = np.zeros(max(n, 1), np.int64)
+    gid = np.zeros(max(n, 1), np.int32)
+    n2 = lib().orc_pairs(_ptr(g), _ptr(offsets), gp, width, height, _ptr(pix), _ptr(gid), n)
+    assert n2 == n
+    return pix[:n], gid[:n]

@@ -436,3 +436,31 @@ int orc_rasterize(int64_t n, const orc_gauss *g, const int64_t *offsets,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Included pairs (for the differentiable FP64 restatement in grad.py)         */
+/* ------------------------------------------------------------------------- */
+
+int64_t orc_pairs(const orc_gauss *g, const int64_t *offsets, const int32_t *gids,
+                  int width, int height, int64_t *out_pixel, int32_t *out_gid,
+                  int64_t cap)
+{
+    const int tiles_x = (width + ORC_TILE - 1) / ORC_TILE;
+    const int tiles_y = (height + ORC_TILE - 1) / ORC_TILE;
+    int64_t k = 0;
+    for (int t = 0; t < tiles_x * tiles_y; ++t) {
+        const int tx = t % tiles_x, ty = t / tiles_x;
+        for (int py = ty * ORC_TILE; py < (ty + 1) * ORC_TILE && py < height; ++py)
+            for (int px = tx * ORC_TILE; px < (tx + 1) * ORC_TILE && px < width; ++px)
+                for (int64_t j = offsets[t]; j < offsets[t + 1]; ++j) {
+                    if (!orc_includes(g + gids[j], px, py)) continue;
+                    if (out_pixel && out_gid) {
+                        if (k >= cap) return -1;
+                        out_pixel[k] = (int64_t)py * width + px;
+                        out_gid[k] = gids[j];
+                    }
+                    ++k;
+                }
+    }
+    return k;
+}

@@ -110,6 +110,13 @@ int orc_rasterize(int64_t n, const orc_gauss *g, const int64_t *offsets,
                   const double bg[3], int tile_begin, int tile_end,
                   double *out_rgb, double *out_aux, int32_t *out_count);
 
+/* All included (pixel, Gaussian) pairs: pixel index py * width + px and
+ * Gaussian index, tile by tile, pixel by pixel, list order.  Returns the
+ * number of pairs, or -1 if it exceeds cap (outputs may be NULL to count). */
+int64_t orc_pairs(const orc_gauss *g, const int64_t *offsets, const int32_t *gids,
+                  int width, int height, int64_t *out_pixel, int32_t *out_gid,
+                  int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif

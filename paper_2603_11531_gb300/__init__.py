@@ -38,8 +38,9 @@ EXPORTS = (
     "mgs_workspace_reserve", "mgs_workspace_bytes", "mgs_workspace_sync", "mgs_render",
     "mgs_render_checked", "mgs_render_to_host", "mgs_tile_lists", "mgs_last_error",
     "mgs_version", "mgs_workspace_set_timing", "mgs_workspace_stage_times",
-    "mgs_render_static",
+    "mgs_render_static", "mgs_render_backward",
 )
+MLP_GRAD_SIZE = 5957
 
 
 class MGSError(RuntimeError):
@@ -103,6 +104,8 @@ def lib():
                 "mgs_workspace_stage_times": ([P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], I32),
                 "mgs_render_static": ([P, I64, I32, ctypes.POINTER(mgs_camera),
                                        ctypes.POINTER(mgs_render_opts), P, P], I32),
+                "mgs_render_backward": ([P, P, ctypes.POINTER(mgs_camera),
+                                         ctypes.POINTER(mgs_render_opts), P, P, P, P, P], I32),
                 "mgs_last_error": ([], ctypes.c_char_p),
                 "mgs_version": ([], ctypes.c_char_p),
             }
@@ -299,6 +302,14 @@ def mgs_render_static(attrs, cam, opts, out_rgb, stream=None):
     c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
     _check(lib().mgs_render_static(_ptr(a), int(a.shape[0]), prec, ctypes.byref(c),
                                    ctypes.byref(opts), _ptr(out_rgb), _stream(stream)))
+
+
+def mgs_render_backward(ws, scene, cam, opts, dL_drgb, aux, d_attrs, d_mlp=None, stream=None):
+    """Adjoint of mgs_render (see include/mobilegs.h); device tensors in/out."""
+    c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    _check(lib().mgs_render_backward(ws, scene, ctypes.byref(c), ctypes.byref(opts),
+                                     _ptr(dL_drgb), _ptr(aux), _ptr(d_attrs), _ptr(d_mlp),
+                                     _stream(stream)))
 
 
 def mgs_version() -> str:

@@ -90,10 +90,15 @@ struct mgs_workspace_s {
     uint2 *rect = nullptr;
     uint32_t *tile_count = nullptr;
     uint32_t *tile_offsets = nullptr;
+    uint32_t *tile_order = nullptr;
     uint32_t *gids = nullptr;
     uint32_t *bases = nullptr;   // [binning CTAs][tiles] block bases
     int64_t bases_cap = 0;
     float *img = nullptr;
+    float *bwd_g = nullptr;        // backward: per-Gaussian raster gradients
+    int64_t bwd_g_cap = 0;
+    float *bwd_partials = nullptr; // backward: per-CTA MLP weight gradients
+    int64_t bwd_partials_cap = 0;
     DevStatus *status = nullptr;
     int64_t last_tiles = 0;
     uint64_t grow_hint = 0;  // pairs needed by an overflowed render
@@ -106,7 +111,7 @@ namespace {
 
 int64_t ws_bytes(const mgs_workspace_s *w) {
     return w->n_cap * (int64_t)(sizeof(ProjRec) + sizeof(uint2)) +
-           w->tiles_cap * 2 * (int64_t)sizeof(uint32_t) + (int64_t)w->pair_cap * 4 +
+           w->tiles_cap * 3 * (int64_t)sizeof(uint32_t) + (int64_t)w->pair_cap * 4 +
            w->img_cap * 12 + w->bases_cap * 4 + (int64_t)sizeof(DevStatus);
 }
 
@@ -123,10 +128,12 @@ mgs_status ws_ensure(mgs_workspace_s *w, int64_t n, int64_t tiles, uint64_t pair
     if (tiles + 1 > w->tiles_cap) {
         dev_free(w->tile_count);
         dev_free(w->tile_offsets);
+        dev_free(w->tile_order);
         w->tiles_cap = 0;
         const size_t t = (size_t)tiles + 1;
         if ((e = dev_alloc(&w->tile_count, t)) != cudaSuccess) return cuda_fail(e, "workspace");
         if ((e = dev_alloc(&w->tile_offsets, t)) != cudaSuccess) return cuda_fail(e, "workspace");
+        if ((e = dev_alloc(&w->tile_order, t)) != cudaSuccess) return cuda_fail(e, "workspace");
         w->tiles_cap = (int64_t)t;
     }
     if (pairs > w->pair_cap) {
@@ -187,15 +194,25 @@ uint64_t default_pairs(int64_t n) {
     return p < (1u << 20) ? (1u << 20) : p;
 }
 
+// Backward request: when non-null, render_impl builds the frame's records and
+// tile lists and then runs the adjoint kernels instead of the rasteriser.
+struct BackwardIO {
+    const float *dL_drgb;
+    const float *aux;
+    float *d_attrs;
+    float *d_mlp;
+};
+
 mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
                        const mgs_render_opts *opts, float *out_rgb, float *out_aux,
-                       int32_t *out_count, cudaStream_t stream) {
+                       int32_t *out_count, cudaStream_t stream,
+                       const BackwardIO *bwd = nullptr) {
     if (!w || !s) return fail(MGS_ERR_INVALID_ARG, "workspace or scene is NULL");
     if (w->ctx != s->ctx) return fail(MGS_ERR_INVALID_ARG, "scene and workspace belong to different contexts");
     mgs_status st = check_camera(cam);
     if (st != MGS_OK) return st;
     if (!opts) return fail(MGS_ERR_INVALID_ARG, "opts is NULL");
-    if (!out_rgb) return fail(MGS_ERR_INVALID_ARG, "out_rgb is NULL");
+    if (!out_rgb && !bwd) return fail(MGS_ERR_INVALID_ARG, "out_rgb is NULL");
     if (opts->use_mlp && !s->has_mlp)
         return fail(MGS_ERR_INVALID_ARG, "use_mlp requested but the scene has no MLP weights");
     for (int k = 0; k < 3; ++k)
@@ -226,6 +243,7 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     a.rect = w->rect;
     a.tile_count = w->tile_count;
     a.tile_offsets = w->tile_offsets;
+    a.tile_order = w->tile_order;
     a.gids = w->gids;
     a.capacity = w->pair_cap;
     a.status = w->status;
@@ -252,7 +270,32 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     if ((e = launch_binning(a, w->ctx->sm_count, w->bases, stream)) != cudaSuccess)
         return cuda_fail(e, "binning launch");
     if (w->timing) cudaEventRecord(ev[2], stream);
-    if ((e = launch_raster(a, stream)) != cudaSuccess) return cuda_fail(e, "raster launch");
+    if (bwd) {
+        if (s->n > w->bwd_g_cap) {
+            dev_free(w->bwd_g);
+            w->bwd_g_cap = 0;
+            if ((e = dev_alloc(&w->bwd_g, (size_t)s->n * grad_record_size())) != cudaSuccess)
+                return cuda_fail(e, "workspace");
+            w->bwd_g_cap = s->n;
+        }
+        const int64_t np = (int64_t)pre_bwd_blocks(s->n, w->ctx->sm_count) * mlp_grad_size();
+        if (np > w->bwd_partials_cap) {
+            dev_free(w->bwd_partials);
+            w->bwd_partials_cap = 0;
+            if ((e = dev_alloc(&w->bwd_partials, (size_t)np)) != cudaSuccess)
+                return cuda_fail(e, "workspace");
+            w->bwd_partials_cap = np;
+        }
+        if (s->n > 0 && (e = launch_backward(a, w->ctx->sm_count, bwd->dL_drgb, bwd->aux, w->bwd_g,
+                                             bwd->d_attrs, bwd->d_mlp, w->bwd_partials,
+                                             stream)) != cudaSuccess)
+            return cuda_fail(e, "backward launch");
+        if (s->n == 0 && bwd->d_mlp &&
+            (e = cudaMemsetAsync(bwd->d_mlp, 0, (size_t)mlp_grad_size() * 4, stream)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+    } else if ((e = launch_raster(a, stream)) != cudaSuccess) {
+        return cuda_fail(e, "raster launch");
+    }
     if (w->timing) {
         cudaEventRecord(ev[3], stream);
         w->pending.push_back(ev);
@@ -411,9 +454,12 @@ mgs_status mgs_workspace_destroy(mgs_workspace w) {
     dev_free(w->rect);
     dev_free(w->tile_count);
     dev_free(w->tile_offsets);
+    dev_free(w->tile_order);
     dev_free(w->gids);
     dev_free(w->bases);
     dev_free(w->img);
+    dev_free(w->bwd_g);
+    dev_free(w->bwd_partials);
     dev_free(w->status);
     for (auto &q : w->pending)
         for (auto x : q) cudaEventDestroy(x);
@@ -490,6 +536,20 @@ mgs_status mgs_render(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
                       int32_t *out_count, mgs_stream stream) {
     return render_impl(w, s, cam, opts, out_rgb, out_aux, out_count,
                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+mgs_status mgs_render_backward(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
+                               const mgs_render_opts *opts, const float *dL_drgb,
+                               const float *aux, float *d_attrs, float *d_mlp,
+                               mgs_stream stream) {
+    if (!dL_drgb || !aux || !d_attrs)
+        return fail(MGS_ERR_INVALID_ARG, "dL_drgb, aux and d_attrs are required");
+    if (opts && opts->use_mlp == 0 && d_mlp == nullptr) {
+        // fine: no MLP gradients requested
+    }
+    BackwardIO io{dL_drgb, aux, d_attrs, d_mlp};
+    return render_impl(w, s, cam, opts, nullptr, nullptr, nullptr,
+                       reinterpret_cast<cudaStream_t>(stream), &io);
 }
 
 mgs_status mgs_render_checked(mgs_workspace w, mgs_scene s, const mgs_camera *cam,

@@ -1,0 +1,654 @@
+// Backward pass: the adjoint of the forward render (Sec. 3.1 Eq. 2-4, Sec. 3.2,
+// App. B), for training through torch.autograd.
+//
+// Per pixel p with C = (1 - T) A / B + T c_bg, r = A / B, G = dL/dC(p):
+//   dL/dc_i  += (1 - T)/B * a_i w_i G
+//   dL/dw_i  += (1 - T)/B * a_i G.(c_i - r)
+//   dL/da_i  += w_i (1 - T)/B G.(c_i - r) - T/(1 - a_i) G.(c_bg - r)
+// and through a_i = o_i exp(-q/2) (zero when the 0.99 clamp is active) to
+// o_i, the pixel mean and the conic.  All of these only need (A, B, T) of the
+// forward, so the backward is as order-independent as the forward.
+//
+//   k_raster_bwd      one CTA per tile, same blocks and culling as the
+//                     forward; per-Gaussian partials are reduced across the
+//                     warp and added to a per-Gaussian gradient record.
+//   k_preprocess_bwd  one thread per Gaussian: recomputes the forward, chains
+//                     through the EWA covariance, projection, SH colour,
+//                     Eq. 3 weight and (warp-cooperatively) the Eq. 4 MLP; MLP
+//                     weight gradients are summed per CTA, then reduced in a
+//                     fixed order by k_mlp_grad_reduce.
+#include "mgs_internal.cuh"
+#include "mgs_mlp.cuh"
+
+namespace mgs {
+namespace {
+
+constexpr int kBwdThreads = 64;   // raster backward: two warps per tile
+constexpr int kGRec = 12;         // per-Gaussian raster gradient record
+// layout: dc(3), dw, do, dm(2), dK(3) [conic A, B, C], pad(2)
+
+__device__ __forceinline__ float ex2f(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
+                                                            const float *__restrict__ dL,
+                                                            const float *__restrict__ aux,
+                                                            float *__restrict__ gG) {
+    __shared__ float4 buf[2][4][32];
+    const DevCamera &cam = args.cam;
+    const int tile = (int)args.tile_order[blockIdx.x];
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx0 = tx * kTile, by0 = ty * kTile + 8 * warp;
+    const int px0 = bx0 + 4 * (lane & 3);
+    const int py = by0 + (lane >> 2);
+    if (args.status->last_pairs > args.capacity) return;
+
+    // per-pixel constants from the forward's (A, B, T) and dL/dC
+    const int64_t HW = (int64_t)cam.width * cam.height;
+    float G[4][3], kA[4], Gr[4], Gbr[4], Tp[4];
+    bool valid[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int x = px0 + k;
+        valid[k] = false;
+        G[k][0] = G[k][1] = G[k][2] = 0.f;
+        kA[k] = Gr[k] = Gbr[k] = Tp[k] = 0.f;
+        if (x < cam.width && py < cam.height) {
+            const int64_t p = (int64_t)py * cam.width + x;
+            const float B = aux[3 * HW + p];
+            if (B > 0.0f) {
+                const float T = aux[4 * HW + p];
+                const float inv = 1.0f / B;
+                float r[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    G[k][ch] = dL[3 * p + ch];
+                    r[ch] = aux[ch * HW + p] * inv;
+                }
+                kA[k] = (1.0f - T) * inv;
+                Gr[k] = G[k][0] * r[0] + G[k][1] * r[1] + G[k][2] * r[2];
+                Gbr[k] = G[k][0] * (args.bg[0] - r[0]) + G[k][1] * (args.bg[1] - r[1]) +
+                         G[k][2] * (args.bg[2] - r[2]);
+                Tp[k] = T;
+                valid[k] = true;
+            }
+        }
+    }
+    const uint32_t start = args.tile_offsets[tile];
+    const uint32_t end = args.tile_offsets[tile + 1];
+    const float bx = (float)bx0 + 8.0f, by = (float)by0 + 4.0f;
+    const float pyc = (float)py + 0.5f;
+    const float kq = -0.72134752044448170f;  // -log2(e) / 2
+    float4(*wb)[32] = buf[warp];
+
+    for (uint32_t base = start; base < end; base += 32) {
+        const uint32_t j = base + lane;
+        bool cand = false;
+        uint32_t gid = 0;
+        float4 a, b, c;
+        if (j < end) {
+            gid = __ldg(&args.gids[j]);
+            a = __ldg(&args.rec[gid].a);
+            b = __ldg(&args.rec[gid].b);
+            c = __ldg(&args.rec[gid].c);
+            cand = block_may_hit(a.x, a.y, a.z, a.w, b.x, bx, by, 7.5f, 3.5f);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (cand) {
+            const int pos = __popc(bal & ((1u << lane) - 1u));
+            const float w = -b.z, o = exp2f(b.y);
+            const float iw = 1.0f / w;
+            wb[0][pos] = a;
+            wb[1][pos] = make_float4(b.x, b.y, o, w);
+            // colour c = (-w c) / (-w); conic (A, B, C) = L L^T from the factors
+            wb[2][pos] = make_float4(-b.w * iw, -c.x * iw, -c.y * iw, a.z * a.z);
+            wb[3][pos] = make_float4(a.z * a.w, a.w * a.w + b.x * b.x, __uint_as_float(gid), 0.f);
+        }
+        __syncwarp();
+        const int nc = __popc(bal);
+        for (int k = 0; k < nc; ++k) {
+            const float4 s0 = wb[0][k], s1 = wb[1][k], s2 = wb[2][k], s3 = wb[3][k];
+            const float mx = s0.x, my = s0.y, l11 = s0.z, l21 = s0.w;
+            const float l22 = s1.x, lo = s1.y, o = s1.z, w = s1.w;
+            const float cr = s2.x, cg = s2.y, cb = s2.z, cA = s2.w, cB = s3.x, cC = s3.y;
+            float acc[10];
+#pragma unroll
+            for (int e = 0; e < 10; ++e) acc[e] = 0.f;
+            const float dy = __fsub_rn(pyc, my);
+            const float ldy = __fmul_rn(l21, dy);
+            const float e2 = __fmul_rn(l22, dy);
+            const float e2s = __fmul_rn(e2, e2);
+#pragma unroll
+            for (int px = 0; px < 4; ++px) {
+                const float dx = __fsub_rn((float)(px0 + px) + 0.5f, mx);
+                const float e1 = __fmaf_rn(l11, dx, ldy);
+                const float q = __fmaf_rn(e1, e1, e2s);
+                if (!valid[px] || !(q <= 9.0f)) continue;
+                const float araw = ex2f(__fmaf_rn(q, kq, lo));
+                const float al = fminf(araw, 0.99f);
+                const float Gc = G[px][0] * cr + G[px][1] * cg + G[px][2] * cb;
+                const float gal = w * kA[px] * (Gc - Gr[px]) - Tp[px] / (1.0f - al) * Gbr[px];
+                const float kc = kA[px] * al * w;
+                acc[0] += kc * G[px][0];
+                acc[1] += kc * G[px][1];
+                acc[2] += kc * G[px][2];
+                acc[3] += kA[px] * al * (Gc - Gr[px]);
+                if (araw < 0.99f && o > 0.0f) {
+                    acc[4] += gal * (al / o);
+                    const float gq = -0.5f * al * gal;
+                    acc[5] += -2.0f * gq * (cA * dx + cB * dy);
+                    acc[6] += -2.0f * gq * (cB * dx + cC * dy);
+                    acc[7] += gq * dx * dx;
+                    acc[8] += 2.0f * gq * dx * dy;
+                    acc[9] += gq * dy * dy;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 10; ++e) acc[e] = warp_sum(acc[e]);
+            if (lane == 0) {
+                float *dst = gG + (size_t)__float_as_uint(s3.z) * kGRec;
+#pragma unroll
+                for (int e = 0; e < 10; ++e) atomicAdd(dst + e, acc[e]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Preprocessing adjoint.
+// ---------------------------------------------------------------------------
+
+constexpr int kDStride = 65;  // floats per per-row delta buffer (conflict-free)
+constexpr int kMlpGrad = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden +
+                         kMlpHidden + kMlpOut * kMlpHidden + kMlpOut;  // 5957
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kMlpHidden * kMlpIn, kOffW2 = kOffB1 + kMlpHidden,
+              kOffB2 = kOffW2 + kMlpHidden * kMlpHidden, kOffW3 = kOffB2 + kMlpHidden,
+              kOffB3 = kOffW3 + kMlpOut * kMlpHidden;
+
+struct BwdSmem {
+    MlpSmem mlp;
+    __nv_bfloat16 h1[kMlpThreads / 32][32 * kHStride];
+    __nv_bfloat16 h2[kMlpThreads / 32][32 * kHStride];
+    float d2[kMlpThreads / 32][32 * kDStride];
+    float d1[kMlpThreads / 32][32 * kDStride];
+    float d3[kMlpThreads / 32][32 * 8];
+    float acc[kMlpGrad];
+};
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <bool kFP16>
+__device__ __forceinline__ void load_rec(const void *attrs, int64_t i, float (&v)[kRec]) {
+    if constexpr (kFP16) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(attrs) + 3 * i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 u = __ldg(p + k);
+            const __half2 *h = reinterpret_cast<const __half2 *>(&u);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 f = __half22float2(h[j]);
+                v[8 * k + 2 * j] = f.x;
+                v[8 * k + 2 * j + 1] = f.y;
+            }
+        }
+    } else {
+        const float4 *p = reinterpret_cast<const float4 *>(attrs) + 6 * i;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 f = __ldg(p + k);
+            v[4 * k] = f.x;
+            v[4 * k + 1] = f.y;
+            v[4 * k + 2] = f.z;
+            v[4 * k + 3] = f.w;
+        }
+    }
+}
+
+template <bool kFP16, bool kMLP, bool kResidual>
+__global__ void __launch_bounds__(kMlpThreads) k_preprocess_bwd(RenderArgs args,
+                                                               const float *__restrict__ gG,
+                                                               float *__restrict__ d_attrs,
+                                                               float *__restrict__ partials) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BwdSmem &sm = *reinterpret_cast<BwdSmem *>(smem_raw);
+    const DevCamera &cam = args.cam;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (kMLP) {
+        mlp_load_weights(sm.mlp, args.mlp);
+        for (int e = threadIdx.x; e < kMlpGrad; e += blockDim.x) sm.acc[e] = 0.f;
+        __syncthreads();
+    }
+    const float *W = cam.R;
+    float cc[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cc[j] = -(W[j] * cam.t[0] + W[3 + j] * cam.t[1] + W[6 + j] * cam.t[2]);
+    const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f;
+    const float limx = 1.3f * (0.5f * (float)cam.width / cam.fx);
+    const float limy = 1.3f * (0.5f * (float)cam.height / cam.fy);
+
+    for (int64_t base = (int64_t)blockIdx.x * kMlpThreads; base < args.n;
+         base += (int64_t)gridDim.x * kMlpThreads) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < args.n;
+        float v[kRec];
+#pragma unroll
+        for (int k = 0; k < kRec; ++k) v[k] = 0.f;
+        bool vis = false;
+        if (valid) {
+            load_rec<kFP16>(args.attrs, i, v);
+            const uint2 r = args.rect[i];
+            vis = (r.x != 0u || r.y != 0u) && ((r.x >> 16) > (r.x & 0xFFFF));
+        }
+        float up[10];
+#pragma unroll
+        for (int e = 0; e < 10; ++e) up[e] = vis ? gG[(size_t)i * kGRec + e] : 0.f;
+        // ---- forward recompute (FP32) ----
+        const float qn = sqrtf(v[6] * v[6] + v[7] * v[7] + v[8] * v[8] + v[9] * v[9]);
+        const float iqn = vis ? 1.0f / qn : 0.f;
+        const float qw = v[6] * iqn, qx = v[7] * iqn, qy = v[8] * iqn, qz = v[9] * iqn;
+        float d[3] = {v[0] - cc[0], v[1] - cc[1], v[2] - cc[2]};
+        const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const float idn = dn > 0.f ? 1.0f / dn : 0.f;
+        const float P[3] = {d[0] * idn, d[1] * idn, d[2] * idn};
+
+        float phi = 1.0f, o = v[10], yv[5] = {1.f, 0.f, 0.f, 0.f, 0.f};
+        if constexpr (kMLP) {
+            __nv_bfloat16 *xr = &sm.mlp.x[warp][lane * kXStride];
+            float f[kMlpK1];
+#pragma unroll
+            for (int k = 0; k < kMlpK1; ++k) f[k] = 0.f;
+            if (valid) {
+                f[0] = P[0]; f[1] = P[1]; f[2] = P[2];
+                f[3] = v[3]; f[4] = v[4]; f[5] = v[5];
+                f[6] = qw; f[7] = qx; f[8] = qy; f[9] = qz;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) f[10 + k] = v[11 + k];
+            }
+#pragma unroll
+            for (int k = 0; k < kMlpK1; k += 8) {
+                uint4 u;
+                u.x = pack_bf16(f[k], f[k + 1]);
+                u.y = pack_bf16(f[k + 2], f[k + 3]);
+                u.z = pack_bf16(f[k + 4], f[k + 5]);
+                u.w = pack_bf16(f[k + 6], f[k + 7]);
+                *reinterpret_cast<uint4 *>(xr + k) = u;
+            }
+            __syncwarp();
+            mlp_warp<true>(sm.mlp, warp, lane, sm.h1[warp], sm.h2[warp]);
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 5; ++k) yv[k] = sm.mlp.out[warp][lane][k];
+            phi = fmaxf(yv[0], 0.f);
+            o = 1.0f / (1.0f + __expf(-yv[1]));
+        }
+        // colour
+        float cbase[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            cbase[ch] = C0 * v[11 + ch] - C1 * P[1] * v[14 + ch] + C1 * P[2] * v[17 + ch] -
+                       C1 * P[0] * v[20 + ch] + 0.5f;
+            if constexpr (kResidual) cbase[ch] += yv[2 + ch];
+        }
+        // projection
+        float R[9];
+        R[0] = 1.f - 2.f * (qy * qy + qz * qz);
+        R[1] = 2.f * (qx * qy - qw * qz);
+        R[2] = 2.f * (qx * qz + qw * qy);
+        R[3] = 2.f * (qx * qy + qw * qz);
+        R[4] = 1.f - 2.f * (qx * qx + qz * qz);
+        R[5] = 2.f * (qy * qz - qw * qx);
+        R[6] = 2.f * (qx * qz - qw * qy);
+        R[7] = 2.f * (qy * qz + qw * qx);
+        R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+        float t[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) t[r] = W[3 * r] * v[0] + W[3 * r + 1] * v[1] + W[3 * r + 2] * v[2] + cam.t[r];
+        const float rz = vis ? 1.0f / t[2] : 0.f;
+        const float u = t[0] * rz, vv = t[1] * rz;
+        const bool cx_ = fabsf(u) > limx, cy_ = fabsf(vv) > limy;
+        const float uc = fminf(fmaxf(u, -limx), limx), vc = fminf(fmaxf(vv, -limy), limy);
+        const float J00 = cam.fx * rz, J02 = -cam.fx * uc * rz;
+        const float J11 = cam.fy * rz, J12 = -cam.fy * vc * rz;
+        float T0[3], T1[3], M[9], V0[3], V1[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T0[j] = J00 * W[j] + J02 * W[6 + j];
+            T1[j] = J11 * W[3 + j] + J12 * W[6 + j];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) M[3 * k + j] = R[3 * k + j] * v[3 + j];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            V0[j] = T0[0] * M[j] + T0[1] * M[3 + j] + T0[2] * M[6 + j];
+            V1[j] = T1[0] * M[j] + T1[1] * M[3 + j] + T1[2] * M[6 + j];
+        }
+        const float ca = V0[0] * V0[0] + V0[1] * V0[1] + V0[2] * V0[2] + 0.3f;
+        const float cbv = V0[0] * V1[0] + V0[1] * V1[1] + V0[2] * V1[2];
+        const float ccv = V1[0] * V1[0] + V1[1] * V1[1] + V1[2] * V1[2] + 0.3f;
+        const float det = ca * ccv - cbv * cbv;
+        const float idet = vis ? 1.0f / det : 0.f;
+        const float KA = ccv * idet, KB = -cbv * idet, KC = ca * idet;
+        int am = 0;
+        float smax = v[3];
+        if (v[4] > smax) { smax = v[4]; am = 1; }
+        if (v[5] > smax) { smax = v[5]; am = 2; }
+        const float es = vis ? expf(smax * rz) : 0.f;
+
+        // ---- backward ----
+        const float gcol[3] = {up[0], up[1], up[2]}, gw = up[3], go = up[4];
+        float dt[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+        float dP[3] = {0.f, 0.f, 0.f}, dY[12];
+        // conic -> Sigma_2D:  dSigma = -K Gk K, Gk = [[gA, gB/2], [gB/2, gC]]
+        const float G00 = up[7], G01 = 0.5f * up[8], G11 = up[9];
+        const float KG00 = KA * G00 + KB * G01, KG01 = KA * G01 + KB * G11;
+        const float KG10 = KB * G00 + KC * G01, KG11 = KB * G01 + KC * G11;
+        const float dS00 = -(KG00 * KA + KG01 * KB), dS01 = -(KG00 * KB + KG01 * KC);
+        const float dS11 = -(KG10 * KB + KG11 * KC);
+        const float ga = dS00, gb = 2.0f * dS01, gc = dS11;
+        float dV0[3], dV1[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            dV0[j] = 2.0f * ga * V0[j] + gb * V1[j];
+            dV1[j] = gb * V0[j] + 2.0f * gc * V1[j];
+        }
+        float dT0[3], dT1[3], dR[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dT0[k] = dV0[0] * M[3 * k] + dV0[1] * M[3 * k + 1] + dV0[2] * M[3 * k + 2];
+            dT1[k] = dV1[0] * M[3 * k] + dV1[1] * M[3 * k + 1] + dV1[2] * M[3 * k + 2];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float dM = T0[k] * dV0[j] + T1[k] * dV1[j];
+                dR[3 * k + j] = dM * v[3 + j];
+                ds[j] += dM * R[3 * k + j];
+            }
+        }
+        const float dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
+        const float dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
+        const float dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
+        const float dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
+        const float rz2 = rz * rz;
+        dt[2] += -dJ00 * cam.fx * rz2 - dJ11 * cam.fy * rz2;
+        if (!cx_) {
+            dt[0] += -dJ02 * cam.fx * rz2;
+            dt[2] += dJ02 * 2.0f * cam.fx * t[0] * rz2 * rz;
+        } else {
+            dt[2] += dJ02 * cam.fx * uc * rz2;
+        }
+        if (!cy_) {
+            dt[1] += -dJ12 * cam.fy * rz2;
+            dt[2] += dJ12 * 2.0f * cam.fy * t[1] * rz2 * rz;
+        } else {
+            dt[2] += dJ12 * cam.fy * vc * rz2;
+        }
+        // pixel mean
+        dt[0] += up[5] * cam.fx * rz;
+        dt[1] += up[6] * cam.fy * rz;
+        dt[2] += -(up[5] * cam.fx * t[0] + up[6] * cam.fy * t[1]) * rz2;
+        // Eq. 3
+        const float dphi = gw * (2.0f * phi + rz2);
+        dt[2] += gw * (-2.0f * phi * rz2 * rz - es * smax * rz2);
+        ds[am] += gw * es * rz;
+        // colour
+        float dbase[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            dbase[ch] = cbase[ch] > 0.0f ? gcol[ch] : 0.0f;
+            dY[ch] = C0 * dbase[ch];
+            dY[3 + ch] = -C1 * P[1] * dbase[ch];
+            dY[6 + ch] = C1 * P[2] * dbase[ch];
+            dY[9 + ch] = -C1 * P[0] * dbase[ch];
+            dP[0] += -C1 * v[20 + ch] * dbase[ch];
+            dP[1] += -C1 * v[14 + ch] * dbase[ch];
+            dP[2] += C1 * v[17 + ch] * dbase[ch];
+        }
+        float d_o_stored = 0.0f;
+        float dqh[4] = {0.f, 0.f, 0.f, 0.f};
+        if constexpr (kMLP) {
+            // Eq. 4 head: phi = ReLU(y0), o = sigmoid(y1), residual y2..4
+            float d3[5];
+            d3[0] = yv[0] > 0.0f ? dphi : 0.0f;
+            d3[1] = go * o * (1.0f - o);
+            d3[2] = kResidual ? dbase[0] : 0.0f;
+            d3[3] = kResidual ? dbase[1] : 0.0f;
+            d3[4] = kResidual ? dbase[2] : 0.0f;
+            if (!vis) d3[0] = d3[1] = d3[2] = d3[3] = d3[4] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) sm.d3[warp][lane * 8 + k] = d3[k];
+            const __nv_bfloat16 *h1 = &sm.h1[warp][lane * kHStride];
+            const __nv_bfloat16 *h2 = &sm.h2[warp][lane * kHStride];
+            float *d2 = &sm.d2[warp][lane * kDStride];
+            float *d1 = &sm.d1[warp][lane * kDStride];
+            for (int jj = 0; jj < kMlpHidden; ++jj) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) acc += bf(sm.mlp.w3[k * kW2Stride + jj]) * d3[k];
+                d2[jj] = bf(h2[jj]) > 0.0f ? acc : 0.0f;
+            }
+            float dh1[kMlpHidden];
+#pragma unroll
+            for (int ii = 0; ii < kMlpHidden; ++ii) dh1[ii] = 0.f;
+            for (int jj = 0; jj < kMlpHidden; ++jj) {
+                const float dj = d2[jj];
+                const __nv_bfloat16 *wr = &sm.mlp.w2[jj * kW2Stride];
+#pragma unroll
+                for (int ii = 0; ii < kMlpHidden; ++ii) dh1[ii] += bf(wr[ii]) * dj;
+            }
+            float dx[kMlpIn];
+#pragma unroll
+            for (int f = 0; f < kMlpIn; ++f) dx[f] = 0.f;
+#pragma unroll
+            for (int ii = 0; ii < kMlpHidden; ++ii) {
+                const float di = bf(h1[ii]) > 0.0f ? dh1[ii] : 0.0f;
+                d1[ii] = di;
+                const __nv_bfloat16 *wr = &sm.mlp.w1[ii * kW1Stride];
+#pragma unroll
+                for (int f = 0; f < kMlpIn; ++f) dx[f] += bf(wr[f]) * di;
+            }
+            __syncwarp();
+            // weight gradients of this warp's 32 rows -> CTA accumulators
+            {
+                const int j0 = 2 * lane;
+                float a2[2][kMlpHidden];
+#pragma unroll
+                for (int ii = 0; ii < kMlpHidden; ++ii) a2[0][ii] = a2[1][ii] = 0.f;
+                float a1[2][kMlpIn];
+#pragma unroll
+                for (int f = 0; f < kMlpIn; ++f) a1[0][f] = a1[1][f] = 0.f;
+                float a3[5][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                float sb1[2] = {0.f, 0.f}, sb2[2] = {0.f, 0.f}, sb3 = 0.f;
+                for (int r = 0; r < 32; ++r) {
+                    const float e0 = sm.d2[warp][r * kDStride + j0];
+                    const float e1 = sm.d2[warp][r * kDStride + j0 + 1];
+                    const float f0 = sm.d1[warp][r * kDStride + j0];
+                    const float f1 = sm.d1[warp][r * kDStride + j0 + 1];
+                    const __nv_bfloat16 *h1r = &sm.h1[warp][r * kHStride];
+                    const __nv_bfloat16 *xr = &sm.mlp.x[warp][r * kXStride];
+#pragma unroll
+                    for (int ii = 0; ii < kMlpHidden; ++ii) {
+                        const float hv = bf(h1r[ii]);
+                        a2[0][ii] += e0 * hv;
+                        a2[1][ii] += e1 * hv;
+                    }
+#pragma unroll
+                    for (int f = 0; f < kMlpIn; ++f) {
+                        const float xv = bf(xr[f]);
+                        a1[0][f] += f0 * xv;
+                        a1[1][f] += f1 * xv;
+                    }
+                    const float h20 = bf(sm.h2[warp][r * kHStride + j0]);
+                    const float h21 = bf(sm.h2[warp][r * kHStride + j0 + 1]);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        const float dk = sm.d3[warp][r * 8 + k];
+                        a3[k][0] += dk * h20;
+                        a3[k][1] += dk * h21;
+                    }
+                    sb1[0] += f0;
+                    sb1[1] += f1;
+                    sb2[0] += e0;
+                    sb2[1] += e1;
+                    if (lane < 5) sb3 += sm.d3[warp][r * 8 + lane];
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                    for (int ii = 0; ii < kMlpHidden; ++ii)
+                        atomicAdd(&sm.acc[kOffW2 + (j0 + h) * kMlpHidden + ii], a2[h][ii]);
+#pragma unroll
+                    for (int f = 0; f < kMlpIn; ++f)
+                        atomicAdd(&sm.acc[kOffW1 + (j0 + h) * kMlpIn + f], a1[h][f]);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k)
+                        atomicAdd(&sm.acc[kOffW3 + k * kMlpHidden + j0 + h], a3[k][h]);
+                    atomicAdd(&sm.acc[kOffB1 + j0 + h], sb1[h]);
+                    atomicAdd(&sm.acc[kOffB2 + j0 + h], sb2[h]);
+                }
+                if (lane < 5) atomicAdd(&sm.acc[kOffB3 + lane], sb3);
+            }
+            __syncwarp();
+            dP[0] += dx[0];
+            dP[1] += dx[1];
+            dP[2] += dx[2];
+            ds[0] += dx[3];
+            ds[1] += dx[4];
+            ds[2] += dx[5];
+            dqh[0] += dx[6];
+            dqh[1] += dx[7];
+            dqh[2] += dx[8];
+            dqh[3] += dx[9];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) dY[k] += dx[10 + k];
+        } else {
+            d_o_stored = go;
+            (void)dphi;
+        }
+        if (!valid) continue;
+        float *out = d_attrs + (size_t)i * kRec;
+        if (!vis) {
+#pragma unroll
+            for (int k = 0; k < kRec; ++k) out[k] = 0.f;
+            continue;
+        }
+        // R(q_hat) -> q_hat
+        const float w_ = qw, x_ = qx, y_ = qy, z_ = qz;
+        dqh[0] += 2.f * (-z_ * dR[1] + y_ * dR[2] + z_ * dR[3] - x_ * dR[5] - y_ * dR[6] + x_ * dR[7]);
+        dqh[1] += 2.f * (y_ * dR[1] + z_ * dR[2] + y_ * dR[3] - 2.f * x_ * dR[4] - w_ * dR[5] +
+                         z_ * dR[6] + w_ * dR[7] - 2.f * x_ * dR[8]);
+        dqh[2] += 2.f * (-2.f * y_ * dR[0] + x_ * dR[1] + w_ * dR[2] + x_ * dR[3] + z_ * dR[5] -
+                         w_ * dR[6] + z_ * dR[7] - 2.f * y_ * dR[8]);
+        dqh[3] += 2.f * (-2.f * z_ * dR[0] - w_ * dR[1] + x_ * dR[2] + w_ * dR[3] - 2.f * z_ * dR[4] +
+                         y_ * dR[5] + x_ * dR[6] + y_ * dR[7]);
+        const float qd = qw * dqh[0] + qx * dqh[1] + qy * dqh[2] + qz * dqh[3];
+        dq[0] = (dqh[0] - qw * qd) * iqn;
+        dq[1] = (dqh[1] - qx * qd) * iqn;
+        dq[2] = (dqh[2] - qy * qd) * iqn;
+        dq[3] = (dqh[3] - qz * qd) * iqn;
+        // t = W mu + t_cam, P = (mu - c) / |mu - c|
+        const float pd = P[0] * dP[0] + P[1] * dP[1] + P[2] * dP[2];
+        float dmu[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            dmu[j] = W[j] * dt[0] + W[3 + j] * dt[1] + W[6 + j] * dt[2] + (dP[j] - P[j] * pd) * idn;
+        out[0] = dmu[0];
+        out[1] = dmu[1];
+        out[2] = dmu[2];
+        out[3] = ds[0];
+        out[4] = ds[1];
+        out[5] = ds[2];
+        out[6] = dq[0];
+        out[7] = dq[1];
+        out[8] = dq[2];
+        out[9] = dq[3];
+        out[10] = d_o_stored;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[11 + k] = dY[k];
+        out[23] = 0.f;
+    }
+    if constexpr (kMLP) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kMlpGrad; e += blockDim.x)
+            partials[(size_t)blockIdx.x * kMlpGrad + e] = sm.acc[e];
+    }
+}
+
+__global__ void k_mlp_grad_reduce(const float *__restrict__ partials, int nparts,
+                                  float *__restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kMlpGrad) return;
+    float s = 0.f;
+    for (int c = 0; c < nparts; ++c) s += partials[(size_t)c * kMlpGrad + e];
+    out[e] = s;
+}
+
+template <bool kFP16, bool kMLP, bool kRes>
+cudaError_t launch_pre_bwd(const RenderArgs &a, int blocks, const float *gG, float *d_attrs,
+                           float *partials, cudaStream_t stream) {
+    const size_t smem = kMLP ? sizeof(BwdSmem) : 16;
+    auto kern = k_preprocess_bwd<kFP16, kMLP, kRes>;
+    if (kMLP) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<blocks, kMlpThreads, smem, stream>>>(a, gG, d_attrs, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int mlp_grad_size() { return kMlpGrad; }
+int grad_record_size() { return kGRec; }
+int pre_bwd_blocks(int64_t n, int sm_count) {
+    int64_t b = (n + kMlpThreads - 1) / kMlpThreads;
+    const int64_t cap = 2 * (int64_t)sm_count;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+cudaError_t launch_backward(const RenderArgs &a, int sm_count, const float *dL_drgb,
+                            const float *aux, float *gG, float *d_attrs, float *d_mlp,
+                            float *partials, cudaStream_t stream) {
+    const int T = a.cam.tiles_x * a.cam.tiles_y;
+    cudaError_t e = cudaMemsetAsync(gG, 0, (size_t)a.n * kGRec * sizeof(float), stream);
+    if (e != cudaSuccess) return e;
+    k_raster_bwd<<<T, kBwdThreads, 0, stream>>>(a, dL_drgb, aux, gG);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int blocks = pre_bwd_blocks(a.n, sm_count);
+    const bool fp16 = a.precision == MGS_PREC_FP16;
+    if (a.use_mlp) {
+        if (a.rgb_residual)
+            e = fp16 ? launch_pre_bwd<true, true, true>(a, blocks, gG, d_attrs, partials, stream)
+                     : launch_pre_bwd<false, true, true>(a, blocks, gG, d_attrs, partials, stream);
+        else
+            e = fp16 ? launch_pre_bwd<true, true, false>(a, blocks, gG, d_attrs, partials, stream)
+                     : launch_pre_bwd<false, true, false>(a, blocks, gG, d_attrs, partials, stream);
+        if (e != cudaSuccess) return e;
+        if (d_mlp) {
+            k_mlp_grad_reduce<<<(kMlpGrad + 255) / 256, 256, 0, stream>>>(partials, blocks, d_mlp);
+            e = cudaGetLastError();
+        }
+        return e;
+    }
+    e = fp16 ? launch_pre_bwd<true, false, false>(a, blocks, gG, d_attrs, partials, stream)
+             : launch_pre_bwd<false, false, false>(a, blocks, gG, d_attrs, partials, stream);
+    if (e == cudaSuccess && d_mlp)
+        e = cudaMemsetAsync(d_mlp, 0, (size_t)kMlpGrad * sizeof(float), stream);
+    return e;
+}
+
+}  // namespace mgs

@@ -189,6 +189,36 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
     }
 }
 
+// Rasterisation order: tiles by decreasing list length (bucketed by
+// floor(log2(length))), so the longest tiles start first and the tail of the
+// launch is made of short tiles.  One block.
+__global__ void __launch_bounds__(kScanThreads) k_tile_order(const uint32_t *__restrict__ count,
+                                                             int T, uint32_t *__restrict__ order) {
+    __shared__ uint32_t hist[33], start[33];
+    const int tid = threadIdx.x;
+    if (tid < 33) hist[tid] = 0u;
+    __syncthreads();
+    for (int t = tid; t < T; t += blockDim.x) {
+        const uint32_t c = count[t];
+        const int b = c ? 32 - __clz(c) : 0;      // 0 (empty) .. 32
+        atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t run = 0;
+        for (int b = 32; b >= 0; --b) {          // longest bucket first
+            start[b] = run;
+            run += hist[b];
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < T; t += blockDim.x) {
+        const uint32_t c = count[t];
+        const int b = c ? 32 - __clz(c) : 0;
+        order[atomicAdd(&start[b], 1u)] = (uint32_t)t;
+    }
+}
+
 }  // namespace
 
 int bin_ctas(int64_t n, int sm_count) {
@@ -217,6 +247,8 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases,
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_scan<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, T, a.capacity, a.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_tile_order<<<1, kScanThreads, 0, stream>>>(a.tile_count, T, a.tile_order);
     if ((e = cudaGetLastError()) != cudaSuccess || a.n == 0) return e;
     k_bin_scatter<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, a.tile_offsets,
                                                     bases, a.gids, a.capacity, a.status);

@@ -74,6 +74,7 @@ struct RenderArgs {
     uint2 *rect;              // packed (x_lo | x_hi << 16, y_lo | y_hi << 16)
     uint32_t *tile_count;     // [T]
     uint32_t *tile_offsets;   // [T + 1]
+    uint32_t *tile_order;     // [T] rasterisation order (longest lists first)
     uint32_t *gids;           // [capacity]
     uint64_t capacity;
     DevStatus *status;
@@ -83,11 +84,37 @@ struct RenderArgs {
     int32_t *out_count;
 };
 
+// Can Gaussian (m, l) include any pixel centre of the block centred at (bx, by)
+// with half extents (hx, hy)?  Sound for the exact FP32 test: the slab bounds
+// |e1| <= 3 and |e2| <= 3 hold for every included pixel, and the margin
+// (2^-18 relative) covers the rounding of both evaluations.
+__device__ __forceinline__ bool block_may_hit(float mx, float my, float l11, float l21, float l22,
+                                              float bx, float by, float hx, float hy) {
+    const float dxb = bx - mx, dyb = by - my;
+    const float e1c = fabsf(fmaf(l11, dxb, l21 * dyb));
+    const float h1 = fmaf(fabsf(l11), hx, fabsf(l21) * hy);
+    const float m1 = 3.814697265625e-06f *
+                     (fabsf(l11) * (fabsf(dxb) + hx) + fabsf(l21) * (fabsf(dyb) + hy) + 4.0f);
+    const float e2c = fabsf(l22 * dyb);
+    const float h2 = fabsf(l22) * hy;
+    const float m2 = 3.814697265625e-06f * (fabsf(l22) * (fabsf(dyb) + hy) + 4.0f);
+    return (e1c - h1 <= 3.0f + m1) && (e2c - h2 <= 3.0f + m2);
+}
+
 // Launchers (each enqueues its kernels on `stream`).
 cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream);
 // Per-tile counts, scan and scatter.  `bases` has bin_ctas(...) * T entries.
 cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases, cudaStream_t stream);
 int bin_ctas(int64_t n, int sm_count);
+// Backward pass (mgs_backward.cu): gG [n][grad_record_size()] scratch,
+// partials [pre_bwd_blocks()][mlp_grad_size()] scratch, d_attrs [n][24],
+// d_mlp [mlp_grad_size()] (nullable).
+cudaError_t launch_backward(const RenderArgs &a, int sm_count, const float *dL_drgb,
+                            const float *aux, float *gG, float *d_attrs, float *d_mlp,
+                            float *partials, cudaStream_t stream);
+int mlp_grad_size();
+int grad_record_size();
+int pre_bwd_blocks(int64_t n, int sm_count);
 // Sets the calling thread's message returned by mgs_last_error().
 void set_last_error(const char *msg);
 cudaError_t launch_raster(const RenderArgs &a, cudaStream_t stream);

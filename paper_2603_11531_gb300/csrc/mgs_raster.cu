@@ -3,8 +3,8 @@
 //   A = sum_i c_i a_i w_i,  B = sum_i a_i w_i,  T = prod_i (1 - a_i)
 //   C = (1 - T) A / B + T c_bg          (foreground term 0 when B = 0)
 //
-// One CTA per 16x16 tile, 128 threads, each thread owning two horizontally
-// adjacent pixels (packed FP32x2 arithmetic).  Each warp owns an 8x8 block and
+// One CTA per 16x16 tile, 64 threads, each thread owning four horizontally
+// adjacent pixels (two packed FP32x2 pairs).  Each warp owns a 16x8 block and
 // walks the tile's Gaussian list itself, testing each entry against its block
 // with a conservative bound and compacting (ballot) the candidates before
 // accumulating them in registers.  No atomics, no sort: every pixel is owned
@@ -14,7 +14,7 @@
 namespace mgs {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 64;
 constexpr int kWarps = kThreads / 32;
 
 typedef unsigned long long f2;  // two packed FP32 lanes
@@ -54,38 +54,64 @@ __device__ __forceinline__ float ex2(float x) {
 //   s2 = {l22, l22, log2 o, log2 o} s3 = {-w, -w, -w c_r, -w c_r}
 //   s4 = {-w c_g, -w c_g, -w c_b, -w c_b}
 
-// Can Gaussian (m, l) include any pixel centre of the block centred at (bx, by)
-// with half extents (hx, hy)?  Sound for the exact FP32 test: the slab bounds
-// |e1| <= 3 and |e2| <= 3 hold for every included pixel, and the margin
-// (2^-18 relative) covers the rounding of both evaluations.
-__device__ __forceinline__ bool block_may_hit(float mx, float my, float l11, float l21, float l22,
-                                              float bx, float by, float hx, float hy) {
-    const float dxb = bx - mx, dyb = by - my;
-    const float e1c = fabsf(fmaf(l11, dxb, l21 * dyb));
-    const float h1 = fmaf(fabsf(l11), hx, fabsf(l21) * hy);
-    const float m1 = 3.814697265625e-06f *
-                     (fabsf(l11) * (fabsf(dxb) + hx) + fabsf(l21) * (fabsf(dyb) + hy) + 4.0f);
-    const float e2c = fabsf(l22 * dyb);
-    const float h2 = fabsf(l22) * hy;
-    const float m2 = 3.814697265625e-06f * (fabsf(l22) * (fabsf(dyb) + hy) + 4.0f);
-    return (e1c - h1 <= 3.0f + m1) && (e2c - h2 <= 3.0f + m2);
+// Accumulates one staged Gaussian into a thread's four pixels (two pairs).
+template <bool kCount>
+__device__ __forceinline__ void accumulate(const ulonglong2 (*wb)[32], int k, f2 pxa, f2 pxb,
+                                           f2 pyc, f2 kq2, f2 (&A)[2][3], f2 (&B)[2],
+                                           f2 (&T)[2], int (&cnt)[4]) {
+    const ulonglong2 s0 = wb[0][k], s1 = wb[1][k], s2 = wb[2][k];
+    // inclusion test (exact FP32 sequence); the row terms are shared by both pairs
+    const f2 dy = sub2(pyc, s0.y);
+    const f2 ldy = mul2(s1.y, dy);
+    const f2 e2 = mul2(s2.x, dy);
+    const f2 e2s = mul2(e2, e2);
+    const f2 dxa = sub2(pxa, s0.x);
+    const f2 dxb = sub2(pxb, s0.x);
+    const f2 e1a = fma2(s1.x, dxa, ldy);
+    const f2 e1b = fma2(s1.x, dxb, ldy);
+    const f2 qa = fma2(e1a, e1a, e2s);
+    const f2 qb = fma2(e1b, e1b, e2s);
+    // a = min(0.99, o 2^(-q log2(e) / 2)), kept negated
+    const f2 ga = fma2(qa, kq2, s2.y);
+    const f2 gb = fma2(qb, kq2, s2.y);
+    float q[4], g[4], n[4];
+    upk(qa, q[0], q[1]);
+    upk(qb, q[2], q[3]);
+    upk(ga, g[0], g[1]);
+    upk(gb, g[2], g[3]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        n[i] = q[i] <= 9.0f ? fmaxf(-ex2(g[i]), -0.99f) : 0.0f;
+        if (kCount) cnt[i] += q[i] <= 9.0f;
+    }
+    const ulonglong2 s3 = wb[3][k], s4 = wb[4][k];
+    const f2 na[2] = {pk(n[0], n[1]), pk(n[2], n[3])};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        A[h][0] = fma2(na[h], s3.y, A[h][0]);
+        A[h][1] = fma2(na[h], s4.x, A[h][1]);
+        A[h][2] = fma2(na[h], s4.y, A[h][2]);
+        B[h] = fma2(na[h], s3.x, B[h]);
+        T[h] = fma2(na[h], T[h], T[h]);
+    }
 }
 
-// One CTA per tile; warp w owns the 8x8 pixel block (w & 1, w >> 1) of the
-// tile, lane l the pixel pair (2 (l & 3), l >> 2) of that block.  Each warp
-// streams the tile's list on its own (no block-wide barrier): 32 entries at a
-// time, one per lane, are fetched, tested against the warp's block, and the
-// candidates are compacted into the warp's shared-memory buffer and then
-// accumulated by all lanes.
+// One CTA (two warps) per tile, tiles launched longest list first; warp w
+// owns the 16x8 pixel block of rows 8w..8w+7, lane l the four pixels
+// (4 (l & 3) .. +3, l >> 2) of that block.  Each warp streams the tile's list
+// on its own (no block-wide barrier): 32 entries at a time, one per lane
+// (the next 32 are fetched while the current ones are accumulated), are
+// tested against the warp's block, compacted into the warp's shared-memory
+// buffer (ballot) and accumulated by all lanes.
 template <bool kAux, bool kCount>
 __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
     __shared__ ulonglong2 buf[kWarps][5][32];
     const DevCamera &cam = args.cam;
-    const int tile = blockIdx.x;
+    const int tile = (int)args.tile_order[blockIdx.x];
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bx0 = tx * kTile + 8 * (warp & 1), by0 = ty * kTile + 8 * (warp >> 1);
-    const int px = bx0 + 2 * (lane & 3);
+    const int bx0 = tx * kTile, by0 = ty * kTile + 8 * warp;
+    const int px = bx0 + 4 * (lane & 3);
     const int py = by0 + (lane >> 2);
 
     if (args.status->last_pairs > args.capacity) return;  // overflowed: lists incomplete
@@ -93,27 +119,36 @@ __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
     const uint32_t start = args.tile_offsets[tile];
     const uint32_t end = args.tile_offsets[tile + 1];
     const bool no_cull = (args.flags & MGS_FLAG_NO_CULL) != 0;
-    const float bx = (float)bx0 + 4.0f, by = (float)by0 + 4.0f;
+    const float bx = (float)bx0 + 8.0f, by = (float)by0 + 4.0f;
 
-    const f2 pxc = pk((float)px + 0.5f, (float)px + 1.5f);
+    const f2 pxa = pk((float)px + 0.5f, (float)px + 1.5f);
+    const f2 pxb = pk((float)px + 2.5f, (float)px + 3.5f);
     const f2 pyc = pk((float)py + 0.5f, (float)py + 0.5f);
     const float kq = -0.72134752044448170f;  // -log2(e) / 2
     const f2 kq2 = pk(kq, kq);
-    f2 Ar = 0ull, Ag = 0ull, Ab = 0ull, B = 0ull;
-    f2 T = pk(1.0f, 1.0f);
-    int cnt0 = 0, cnt1 = 0;
+    f2 A[2][3] = {{0ull, 0ull, 0ull}, {0ull, 0ull, 0ull}};
+    f2 B[2] = {0ull, 0ull};
+    f2 T[2] = {pk(1.0f, 1.0f), pk(1.0f, 1.0f)};
+    int cnt[4] = {0, 0, 0, 0};
     ulonglong2(*wb)[32] = buf[warp];
 
+    float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f), b_n = a_n, c_n = a_n;
+    if (start + lane < end) {
+        const uint32_t gid = __ldg(&args.gids[start + lane]);
+        a_n = __ldg(&args.rec[gid].a);
+        b_n = __ldg(&args.rec[gid].b);
+        c_n = __ldg(&args.rec[gid].c);
+    }
     for (uint32_t base = start; base < end; base += 32) {
         const uint32_t j = base + lane;
-        bool cand = false;
-        float4 a, b, c;
-        if (j < end) {
-            const uint32_t gid = __ldg(&args.gids[j]);
-            a = __ldg(&args.rec[gid].a);
-            b = __ldg(&args.rec[gid].b);
-            c = __ldg(&args.rec[gid].c);
-            cand = no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bx, by, 3.5f, 3.5f);
+        const float4 a = a_n, b = b_n, c = c_n;
+        const bool cand =
+            j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bx, by, 7.5f, 3.5f));
+        if (j + 32 < end) {
+            const uint32_t gid = __ldg(&args.gids[j + 32]);
+            a_n = __ldg(&args.rec[gid].a);
+            b_n = __ldg(&args.rec[gid].b);
+            c_n = __ldg(&args.rec[gid].c);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         if (cand) {
@@ -125,51 +160,26 @@ __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
             wb[4][pos] = make_ulonglong2(pk(c.x, c.x), pk(c.y, c.y));
         }
         __syncwarp();
-        const int n = __popc(bal);
+        const int nc = __popc(bal);
 #pragma unroll 2
-        for (int k = 0; k < n; ++k) {
-            const ulonglong2 s0 = wb[0][k], s1 = wb[1][k], s2 = wb[2][k];
-            // inclusion test (exact FP32 sequence)
-            const f2 dx = sub2(pxc, s0.x);
-            const f2 dy = sub2(pyc, s0.y);
-            const f2 e1 = fma2(s1.x, dx, mul2(s1.y, dy));
-            const f2 e2 = mul2(s2.x, dy);
-            const f2 q = fma2(e1, e1, mul2(e2, e2));
-            // a = min(0.99, o 2^(-q log2(e) / 2)), kept negated
-            const f2 arg = fma2(q, kq2, s2.y);
-            float q0, q1, g0, g1;
-            upk(q, q0, q1);
-            upk(arg, g0, g1);
-            float n0 = fmaxf(-ex2(g0), -0.99f);
-            float n1 = fmaxf(-ex2(g1), -0.99f);
-            n0 = q0 <= 9.0f ? n0 : 0.0f;
-            n1 = q1 <= 9.0f ? n1 : 0.0f;
-            if (kCount) {
-                cnt0 += q0 <= 9.0f;
-                cnt1 += q1 <= 9.0f;
-            }
-            const f2 na = pk(n0, n1);
-            const ulonglong2 s3 = wb[3][k], s4 = wb[4][k];
-            Ar = fma2(na, s3.y, Ar);
-            Ag = fma2(na, s4.x, Ag);
-            Ab = fma2(na, s4.y, Ab);
-            B = fma2(na, s3.x, B);
-            T = fma2(na, T, T);
-        }
+        for (int k = 0; k < nc; ++k)
+            accumulate<kCount>(wb, k, pxa, pxb, pyc, kq2, A, B, T, cnt);
         __syncwarp();
     }
 
     if (py >= cam.height) return;
-    float ar[2], ag[2], ab[2], bb[2], tt[2];
-    upk(Ar, ar[0], ar[1]);
-    upk(Ag, ag[0], ag[1]);
-    upk(Ab, ab[0], ab[1]);
-    upk(B, bb[0], bb[1]);
-    upk(T, tt[0], tt[1]);
-    const int cnts[2] = {cnt0, cnt1};
+    float ar[4], ag[4], ab[4], bb[4], tt[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        upk(A[h][0], ar[2 * h], ar[2 * h + 1]);
+        upk(A[h][1], ag[2 * h], ag[2 * h + 1]);
+        upk(A[h][2], ab[2 * h], ab[2 * h + 1]);
+        upk(B[h], bb[2 * h], bb[2 * h + 1]);
+        upk(T[h], tt[2 * h], tt[2 * h + 1]);
+    }
     const int64_t HW = (int64_t)cam.width * cam.height;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {
         const int x = px + k;
         if (x >= cam.width) break;
         const int64_t p = (int64_t)py * cam.width + x;
@@ -185,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
             args.out_aux[3 * HW + p] = bb[k];
             args.out_aux[4 * HW + p] = tt[k];
         }
-        if (kCount) args.out_count[p] = cnts[k];
+        if (kCount) args.out_count[p] = cnt[k];
     }
 }
 

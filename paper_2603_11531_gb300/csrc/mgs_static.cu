@@ -33,7 +33,8 @@ constexpr size_t kRecOff = 0;
 constexpr size_t kRectOff = kRecOff + align256(kMaxGaussians * sizeof(ProjRec));
 constexpr size_t kCountOff = kRectOff + align256(kMaxGaussians * sizeof(uint2));
 constexpr size_t kOffsetsOff = kCountOff + align256((kMaxTiles + 1) * sizeof(uint32_t));
-constexpr size_t kBasesOff = kOffsetsOff + align256((kMaxTiles + 1) * sizeof(uint32_t));
+constexpr size_t kOrderOff = kOffsetsOff + align256((kMaxTiles + 1) * sizeof(uint32_t));
+constexpr size_t kBasesOff = kOrderOff + align256((kMaxTiles + 1) * sizeof(uint32_t));
 constexpr size_t kGidsOff = kBasesOff + align256((size_t)kMaxBinCtas * kMaxTiles * sizeof(uint32_t));
 constexpr size_t kStatusOff = kGidsOff + align256(kMaxPairs * sizeof(uint32_t));
 constexpr size_t kScratchBytes = kStatusOff + align256(sizeof(DevStatus));  // ~27 MiB
@@ -127,6 +128,7 @@ extern "C" mgs_status mgs_render_static(const void *attrs, int64_t n, int32_t pr
     a.rect = reinterpret_cast<uint2 *>(S + kRectOff);
     a.tile_count = reinterpret_cast<uint32_t *>(S + kCountOff);
     a.tile_offsets = reinterpret_cast<uint32_t *>(S + kOffsetsOff);
+    a.tile_order = reinterpret_cast<uint32_t *>(S + kOrderOff);
     a.gids = reinterpret_cast<uint32_t *>(S + kGidsOff);
     a.capacity = (uint64_t)kMaxPairs;
     a.status = reinterpret_cast<DevStatus *>(S + kStatusOff);
