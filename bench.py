@@ -309,6 +309,8 @@ def run_gpu(args):
             "clocks": clocks,
             "peaks": peaks_kind,
         }
+        if world == 1 and not args.no_serving:
+            line["serving"] = run_serving(m, torch, local)
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline_sample()
             cb.pop("seconds", None)
@@ -320,6 +322,101 @@ def run_gpu(args):
     return 0
 
 
+def _pcts(xs):
+    xs = sorted(xs)
+    if not xs:
+        return None, None
+    return (1000.0 * xs[len(xs) // 2], 1000.0 * xs[min(len(xs) - 1, int(round(0.99 * (len(xs) - 1))))])
+
+
+def run_serving(m, torch, local, n_requests=400, slots=8, max_batch=8):
+    """Serving workload: 8 resident scenes (50k..3M Gaussians, FP16, BF16 MLP),
+    requests at 640x480..1920x1080 with random orbit poses.  Measures the plain
+    renderer (one view per launch sequence, one at a time) and the
+    continuous-batching server on the same request stream: saturated views/s
+    and, under Poisson arrivals at 0.5/0.8/0.95 of the plain capacity,
+    p50/p99 arrival-to-completion latency."""
+    from paper_2603_11531_gb300 import synth
+    from paper_2603_11531_gb300.serving import Server, mgs_now
+    scenes = synth.serving_scenes()
+    r = m.Renderer(local)
+    handles = [r.load_scene(sc) for sc in scenes]
+    rng = np.random.default_rng(44)
+    reqs = []
+    for _ in range(n_requests):
+        k = int(rng.integers(len(scenes)))
+        W, H = synth.SERVING_RESOLUTIONS[int(rng.integers(len(synth.SERVING_RESOLUTIONS)))]
+        reqs.append((k, m.camera_struct(synth.random_orbit_camera(rng, W, H))))
+    opts = m.render_opts(use_mlp=True)
+    pool = {}
+    for k, c in reqs:
+        key = (c.width, c.height)
+        pool.setdefault(key, [torch.empty((c.height, c.width, 3), device="cuda")
+                              for _ in range(2 * slots + 2)])
+    stream = torch.cuda.Stream(device=local)
+    # size every (scene, resolution) once (checked renders), then warm up
+    for k, c in reqs:
+        m.mgs_render_checked(r.ws, handles[k], c, opts, pool[(c.width, c.height)][0], None, None, stream)
+
+    def plain_stream(arrivals):
+        lat = []
+        t0 = mgs_now()
+        for (k, c), a in zip(reqs, arrivals):
+            while mgs_now() - t0 < a:
+                pass
+            m.mgs_render(r.ws, handles[k], c, opts, pool[(c.width, c.height)][0], None, None, stream)
+            stream.synchronize()
+            lat.append(mgs_now() - t0 - a)
+        return lat, mgs_now() - t0
+
+    srv = Server(r.ctx, slots=slots, max_batch=max_batch, hbm_budget_bytes=16 << 30)
+    prev_user = {}   # (resolution) -> {buffer index: request index using it}
+
+    def served_stream(arrivals):
+        prev_user.clear()
+        t0 = mgs_now()
+        tickets, used = [], {}
+        for i, ((k, c), a) in enumerate(zip(reqs, arrivals)):
+            key = (c.width, c.height)
+            j = used.get(key, 0)
+            used[key] = j + 1
+            buf = pool[key][j % len(pool[key])]
+            if j >= len(pool[key]):
+                srv.wait(tickets[prev_user[key][j % len(pool[key])]])
+            prev_user.setdefault(key, {})[j % len(pool[key])] = i
+            while mgs_now() - t0 < a:
+                pass
+            tickets.append(srv.submit(handles[k], c, opts, buf))
+        for t in tickets:
+            srv.wait(t)
+        info = [srv.ticket(t) for t in tickets]
+        lat = [x["t_done"] - x["t_submit"] for x in info]
+        return lat, max(x["t_done"] for x in info) - t0
+
+    zero = [0.0] * n_requests
+    _, t_plain = plain_stream(zero)                      # back to back
+    plain_vps = n_requests / t_plain
+    served_stream(zero)                                  # warm the server's graphs
+    lat_sat, t_sat = served_stream(zero)
+    out = {"requests": n_requests, "slots": slots, "max_batch": max_batch,
+           "plain_views_per_s": plain_vps, "served_views_per_s_saturated": n_requests / t_sat,
+           "rates": []}
+    for f in (0.5, 0.8, 0.95):
+        lam = f * plain_vps
+        arr = list(np.cumsum(rng.exponential(1.0 / lam, n_requests)))
+        lp, tp = plain_stream(arr)
+        ls, ts = served_stream(arr)
+        p50p, p99p = _pcts(lp)
+        p50s, p99s = _pcts(ls)
+        out["rates"].append({"load": f, "arrival_views_per_s": lam,
+                             "plain": {"views_per_s": n_requests / tp, "p50_ms": p50p, "p99_ms": p99p},
+                             "served": {"views_per_s": n_requests / ts, "p50_ms": p50s, "p99_ms": p99s}})
+    out["graphs"] = srv.stats()["graphs"]
+    srv.close()
+    r.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,6 +424,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -219,6 +219,46 @@ mgs_status mgs_render_backward(mgs_workspace ws, mgs_scene scene,
                                const float *dL_drgb, const float *aux,
                                float *d_attrs, float *d_mlp, mgs_stream stream);
 
+/* ---- serving: continuous batching of render requests ------------------------ */
+
+typedef struct mgs_server_s *mgs_server;
+
+typedef struct {
+    int32_t slots;             /* views in flight at once (1..64); each slot owns
+                                  a workspace and a stream */
+    int32_t max_batch;         /* views rasterised by one persistent launch (1..64) */
+    int64_t hbm_budget_bytes;  /* device bytes the slots' workspaces may hold */
+} mgs_server_config;
+
+/* Start a server on the context's device.  A worker thread owned by the
+ * server admits queued requests, in arrival order, into free slots while their
+ * estimated scratch fits the budget, runs their preprocessing and binning as
+ * CUDA graphs, rasterises each group admitted together in one persistent
+ * batched launch, and records completion.  Not in the paper: the serving
+ * pattern of the workload. */
+mgs_status mgs_server_create(mgs_ctx ctx, const mgs_server_config *cfg, mgs_server *out);
+/* Finish every queued and running request, then release the server. */
+mgs_status mgs_server_destroy(mgs_server srv);
+/* Queue one view of a resident scene; out_rgb (device, height x width x 3
+ * FP32, caller-owned) must stay valid until the ticket completes.
+ * Thread-safe. */
+mgs_status mgs_server_submit(mgs_server srv, mgs_scene scene, const mgs_camera *cam,
+                             const mgs_render_opts *opts, float *out_rgb, int64_t *ticket);
+/* Wait at most timeout_ms for the ticket: MGS_ERR_TIMEOUT if it is not done,
+ * else the request's own status (MGS_OK, or MGS_ERR_OOM if it can never fit
+ * the budget). */
+mgs_status mgs_server_wait(mgs_server srv, int64_t ticket, double timeout_ms);
+/* A ticket's state (0 queued, 1 running, 2 done), status and steady-clock
+ * timestamps in seconds (same clock as mgs_now): submitted, admitted, done. */
+mgs_status mgs_server_ticket(mgs_server srv, int64_t ticket, int32_t *state, int32_t *result,
+                             double *t_submit, double *t_admit, double *t_done);
+/* Counters: completed, queued and running requests, workspace bytes held,
+ * whether graphs are in use (1) or launches are direct (0). */
+mgs_status mgs_server_stats(mgs_server srv, int64_t *completed, int64_t *queued,
+                            int64_t *running, int64_t *workspace_bytes, int32_t *graphs);
+/* The server's steady clock, in seconds. */
+double mgs_now(void);
+
 /* ---- allocation-free rendering -------------------------------------------- */
 
 /* Renders one view without allocating any device memory, for callers that

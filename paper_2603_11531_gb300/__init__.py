@@ -39,6 +39,8 @@ EXPORTS = (
     "mgs_render_checked", "mgs_render_to_host", "mgs_tile_lists", "mgs_last_error",
     "mgs_version", "mgs_workspace_set_timing", "mgs_workspace_stage_times",
     "mgs_render_static", "mgs_render_backward",
+    "mgs_server_create", "mgs_server_destroy", "mgs_server_submit", "mgs_server_wait",
+    "mgs_server_ticket", "mgs_server_stats", "mgs_now",
 )
 MLP_GRAD_SIZE = 5957
 

@@ -206,13 +206,13 @@ struct BackwardIO {
 mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
                        const mgs_render_opts *opts, float *out_rgb, float *out_aux,
                        int32_t *out_count, cudaStream_t stream,
-                       const BackwardIO *bwd = nullptr) {
+                       const BackwardIO *bwd = nullptr, RenderArgs *prep = nullptr) {
     if (!w || !s) return fail(MGS_ERR_INVALID_ARG, "workspace or scene is NULL");
     if (w->ctx != s->ctx) return fail(MGS_ERR_INVALID_ARG, "scene and workspace belong to different contexts");
     mgs_status st = check_camera(cam);
     if (st != MGS_OK) return st;
     if (!opts) return fail(MGS_ERR_INVALID_ARG, "opts is NULL");
-    if (!out_rgb && !bwd) return fail(MGS_ERR_INVALID_ARG, "out_rgb is NULL");
+    if (!out_rgb && !bwd && !prep) return fail(MGS_ERR_INVALID_ARG, "out_rgb is NULL");
     if (opts->use_mlp && !s->has_mlp)
         return fail(MGS_ERR_INVALID_ARG, "use_mlp requested but the scene has no MLP weights");
     for (int k = 0; k < 3; ++k)
@@ -270,6 +270,11 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     if ((e = launch_binning(a, w->ctx->sm_count, w->bases, stream)) != cudaSuccess)
         return cuda_fail(e, "binning launch");
     if (w->timing) cudaEventRecord(ev[2], stream);
+    if (prep) {
+        *prep = a;
+        w->last_tiles = T;
+        return MGS_OK;
+    }
     if (bwd) {
         if (s->n > w->bwd_g_cap) {
             dev_free(w->bwd_g);
@@ -307,6 +312,20 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
 }  // namespace
 
 void mgs::set_last_error(const char *msg) { g_err = msg; }
+
+mgs_status mgs::prepare_view(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
+                             const mgs_render_opts *opts, float *out_rgb, cudaStream_t stream,
+                             RenderArgs *args_out) {
+    mgs_status st = render_impl(w, s, cam, opts, out_rgb, nullptr, nullptr, stream, nullptr,
+                                args_out);
+    if (st == MGS_OK) args_out->out_rgb = out_rgb;
+    return st;
+}
+
+int mgs::ctx_device(mgs_ctx c) { return c->device; }
+int mgs::ctx_sm_count(mgs_ctx c) { return c->sm_count; }
+int64_t mgs::scene_size(mgs_scene s) { return s->n; }
+mgs_ctx mgs::scene_ctx(mgs_scene s) { return s->ctx; }
 
 extern "C" {
 

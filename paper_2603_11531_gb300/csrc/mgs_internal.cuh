@@ -117,6 +117,20 @@ int grad_record_size();
 int pre_bwd_blocks(int64_t n, int sm_count);
 // Sets the calling thread's message returned by mgs_last_error().
 void set_last_error(const char *msg);
+// Preprocessing and binning of one view into workspace w (no rasterisation,
+// no allocation if the workspace is large enough); *args_out receives the
+// arguments the rasteriser needs.  Stream-ordered, capturable.
+mgs_status prepare_view(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
+                        const mgs_render_opts *opts, float *out_rgb, cudaStream_t stream,
+                        RenderArgs *args_out);
+int ctx_device(mgs_ctx c);
+int ctx_sm_count(mgs_ctx c);
+int64_t scene_size(mgs_scene s);
+mgs_ctx scene_ctx(mgs_scene s);
 cudaError_t launch_raster(const RenderArgs &a, cudaStream_t stream);
+// Persistent rasteriser over the tiles of `nviews` views (views_dev and
+// prefix_dev in device memory; prefix has nviews + 1 entries).
+cudaError_t launch_raster_batch(const RenderArgs *views_dev, const int *prefix_dev, int nviews,
+                                unsigned *counter_dev, int sm_count, cudaStream_t stream);
 
 }  // namespace mgs

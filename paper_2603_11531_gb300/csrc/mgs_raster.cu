@@ -96,25 +96,22 @@ __device__ __forceinline__ void accumulate(const ulonglong2 (*wb)[32], int k, f2
     }
 }
 
-// One CTA (two warps) per tile, tiles launched longest list first; warp w
-// owns the 16x8 pixel block of rows 8w..8w+7, lane l the four pixels
-// (4 (l & 3) .. +3, l >> 2) of that block.  Each warp streams the tile's list
-// on its own (no block-wide barrier): 32 entries at a time, one per lane
-// (the next 32 are fetched while the current ones are accumulated), are
-// tested against the warp's block, compacted into the warp's shared-memory
-// buffer (ballot) and accumulated by all lanes.
+// Rasterises one tile with one CTA (two warps); warp w owns the 16x8 pixel
+// block of rows 8w..8w+7, lane l the four pixels (4 (l & 3) .. +3, l >> 2) of
+// that block.  Each warp streams the tile's list on its own (no block-wide
+// barrier): 32 entries at a time, one per lane (the next 32 are fetched while
+// the current ones are accumulated), are tested against the warp's block,
+// compacted into the warp's shared-memory buffer (ballot) and accumulated by
+// all lanes.
 template <bool kAux, bool kCount>
-__global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
-    __shared__ ulonglong2 buf[kWarps][5][32];
+__device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
+                                            ulonglong2 (*buf)[5][32]) {
     const DevCamera &cam = args.cam;
-    const int tile = (int)args.tile_order[blockIdx.x];
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bx0 = tx * kTile, by0 = ty * kTile + 8 * warp;
     const int px = bx0 + 4 * (lane & 3);
     const int py = by0 + (lane >> 2);
-
-    if (args.status->last_pairs > args.capacity) return;  // overflowed: lists incomplete
 
     const uint32_t start = args.tile_offsets[tile];
     const uint32_t end = args.tile_offsets[tile + 1];
@@ -199,6 +196,42 @@ __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
     }
 }
 
+// One CTA per tile, longest tile lists first.
+template <bool kAux, bool kCount>
+__global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
+    __shared__ ulonglong2 buf[kWarps][5][32];
+    if (args.status->last_pairs > args.capacity) return;  // overflowed: lists incomplete
+    raster_tile<kAux, kCount>(args, (int)args.tile_order[blockIdx.x], buf);
+}
+
+// Persistent, batched: the tiles of several views (different scenes and
+// resolutions) form one work list; resident CTAs pull (view, tile) items from
+// an atomic counter until the list is exhausted.  Items are numbered view by
+// view (prefix[v] = first item of view v), each view's tiles longest first.
+__global__ void __launch_bounds__(kThreads) k_raster_batch(const RenderArgs *__restrict__ views,
+                                                           const int *__restrict__ prefix,
+                                                           int nviews,
+                                                           unsigned *__restrict__ counter) {
+    __shared__ ulonglong2 buf[kWarps][5][32];
+    __shared__ int item_s;
+    const int total = prefix[nviews];
+    for (;;) {
+        if (threadIdx.x == 0) item_s = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= total) return;
+        int lo = 0, hi = nviews - 1;       // last view with prefix[v] <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const RenderArgs &a = views[lo];
+        if (a.status->last_pairs > a.capacity) continue;   // that view overflowed
+        raster_tile<false, false>(a, (int)a.tile_order[item - prefix[lo]], buf);
+    }
+}
+
 template <bool kAux, bool kCount>
 cudaError_t launch_t(const RenderArgs &a, cudaStream_t stream) {
     const int T = a.cam.tiles_x * a.cam.tiles_y;
@@ -214,6 +247,23 @@ cudaError_t launch_raster(const RenderArgs &a, cudaStream_t stream) {
     if (aux) return launch_t<true, false>(a, stream);
     if (cnt) return launch_t<false, true>(a, stream);
     return launch_t<false, false>(a, stream);
+}
+
+}  // namespace mgs
+
+namespace mgs {
+
+cudaError_t launch_raster_batch(const RenderArgs *views_dev, const int *prefix_dev, int nviews,
+                                unsigned *counter_dev, int sm_count, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(counter_dev, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_batch, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    k_raster_batch<<<sm_count * per_sm, kThreads, 0, stream>>>(views_dev, prefix_dev, nviews,
+                                                               counter_dev);
+    return cudaGetLastError();
 }
 
 }  // namespace mgs
