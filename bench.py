@@ -311,6 +311,8 @@ def run_gpu(args):
         }
         if world == 1 and not args.no_serving:
             line["serving"] = run_serving(m, torch, local)
+        if world == 1 and not args.no_large:
+            line["large"] = run_large(m, torch, local)
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline_sample()
             cb.pop("seconds", None)
@@ -417,6 +419,41 @@ def run_serving(m, torch, local, n_requests=400, slots=8, max_batch=8):
     return out
 
 
+def run_large(m, torch, local, frames=3):
+    """6M Gaussians (unbounded distribution, FP16, BF16 MLP) at 3840x2160:
+    the sort-free renderer next to the sorted front-to-back comparator
+    (per-tile depth order by radix sort, 3DGS early termination), same inputs,
+    same GPU.  Per-frame stage times from CUDA events on the launch stream."""
+    from paper_2603_11531_gb300 import synth
+    scene, cam = synth.workload_large_6m()
+    r = m.Renderer(local)
+    h = r.load_scene(scene)
+    out = torch.empty((cam.height, cam.width, 3), device="cuda")
+    stream = torch.cuda.Stream(device=local)
+    res = {"gaussians": scene.n, "resolution": [cam.width, cam.height]}
+    for name, flags in (("sort_free", 0), ("sorted", m.MGS_FLAG_SORTED)):
+        opts = m.render_opts(use_mlp=True, flags=flags)
+        m.mgs_render_checked(r.ws, h, cam, opts, out, None, None, stream)
+        m.mgs_render(r.ws, h, cam, opts, out, None, None, stream)
+        m.mgs_workspace_stage_times(r.ws, stream)
+        m.mgs_workspace_set_timing(r.ws, True)
+        for _ in range(frames):
+            m.mgs_render(r.ws, h, cam, opts, out, None, None, stream)
+        ms, fr = m.mgs_workspace_stage_times(r.ws, stream)
+        m.mgs_workspace_set_timing(r.ws, False)
+        st, pairs = m.mgs_workspace_sync(r.ws, stream, allow_overflow=True)
+        if st != m.MGS_OK:
+            raise RuntimeError("large workload overflowed its tile lists")
+        per = [x / fr for x in ms]
+        res[name] = {"ms_per_frame": sum(per), "preprocess_mlp_ms": per[0], "binning_ms": per[1],
+                     ("sort_and_blend_ms" if flags else "raster_ms"): per[2],
+                     "fps": 1000.0 / sum(per)}
+    res["pairs_per_frame"] = m.mgs_tile_lists(r.ws, stream=stream)[1]
+    res["sorted_over_sort_free_time"] = res["sorted"]["ms_per_frame"] / res["sort_free"]["ms_per_frame"]
+    r.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,6 +462,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -61,8 +61,13 @@ enum { MGS_PREC_FP32 = 0, MGS_PREC_FP16 = 1 };
 
 /* Render flags (mgs_render_opts.flags). */
 enum {
-    MGS_FLAG_NO_CULL = 1u  /* debug: skip the conservative per-warp culling of
+    MGS_FLAG_NO_CULL = 1u, /* debug: skip the conservative per-warp culling of
                               tile lists (the image must not change) */
+    MGS_FLAG_SORTED = 2u   /* comparator, not the paper's method: depth-sort
+                              every tile list (radix sort) and alpha-blend
+                              front to back, C = sum c_i a_i T_i + T c_bg
+                              (App. B, Eq. 11, 3DGS early termination at
+                              T < 1e-4); out_aux must be NULL */
 };
 
 typedef struct mgs_ctx_s *mgs_ctx;

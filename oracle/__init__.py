@@ -56,7 +56,7 @@ class _MLP(ctypes.Structure):
 
 GAUSS_DTYPE = np.dtype([
     ("visible", np.int32), ("rect", np.int32, 4), ("m32", np.float32, 2),
-    ("l32", np.float32, 3), ("mean", np.float64, 2), ("cov", np.float64, 3),
+    ("l32", np.float32, 3), ("tz32", np.float32), ("mean", np.float64, 2), ("cov", np.float64, 3),
     ("conic", np.float64, 3), ("depth", np.float64), ("rgb", np.float64, 3),
     ("opacity", np.float64), ("phi", np.float64), ("weight", np.float64),
     ("dir", np.float64, 3)], align=True)
@@ -86,6 +86,9 @@ def lib():
             L.orc_rasterize.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int,
                                         ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                         P, P, P]
+            L.orc_rasterize_sorted.restype = ctypes.c_int
+            L.orc_rasterize_sorted.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int,
+                                               ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P]
             L.orc_pairs.restype = ctypes.c_int64
             L.orc_pairs.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int64]
             if L.orc_gauss_size() != GAUSS_DTYPE.itemsize:
@@ -221,3 +224,29 @@ def included_pairs(g: np.ndarray, offsets, gids, width: int, height: int):
     n2 = lib().orc_pairs(_ptr(g), _ptr(offsets), gp, width, height, _ptr(pix), _ptr(gid), n)
     assert n2 == n
     return pix[:n], gid[:n]
+
+
+def rasterize_sorted(g: np.ndarray, offsets, gids, width: int, height: int,
+                     bg=(0.0, 0.0, 0.0), tile_range=None, want_count: bool = False):
+    """Comparator: sorted front-to-back alpha blending (App. B, Eq. 11)."""
+    tx, ty = tiles(width, height)
+    t0, t1 = (0, tx * ty) if tile_range is None else tile_range
+    rgb = np.zeros((height, width, 3), np.float64)
+    cnt = np.zeros((height, width), np.int32) if want_count else None
+    bgv = np.ascontiguousarray(np.asarray(bg, np.float64).reshape(3))
+    gids = np.ascontiguousarray(gids, np.int32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    rc = lib().orc_rasterize_sorted(len(g), _ptr(g), _ptr(offsets),
+                                    _ptr(gids if len(gids) else np.zeros(1, np.int32)),
+                                    width, height, _ptr(bgv), t0, t1, _ptr(rgb), _ptr(cnt))
+    if rc != 0:
+        raise MemoryError("orc_rasterize_sorted")
+    return rgb, cnt
+
+
+def render_sorted(attrs, cam, mlp=None, use_mlp=False, rgb_residual=False, bg=(0.0, 0.0, 0.0),
+                  want_count=False, tile_range=None):
+    g = preprocess(attrs, cam, mlp, use_mlp, rgb_residual)
+    offsets, gids = bin_tiles(g, cam.width, cam.height)
+    rgb, cnt = rasterize_sorted(g, offsets, gids, cam.width, cam.height, bg, tile_range, want_count)
+    return dict(gauss=g, offsets=offsets, gids=gids, rgb=rgb, count=cnt)

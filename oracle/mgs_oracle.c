@@ -116,7 +116,8 @@ void orc_mlp_eval(const orc_mlp *mlp, const double x[22], double out[5])
  * Gaussian is visible.
  */
 static int contract_f32(const double *a, const orc_camera *cam, int tiles_x,
-                        int tiles_y, int32_t rect[4], float m[2], float l[3])
+                        int tiles_y, int32_t rect[4], float m[2], float l[3],
+                        float *depth)
 {
     const float mux = (float)a[0], muy = (float)a[1], muz = (float)a[2];
     const float s[3] = {(float)a[3], (float)a[4], (float)a[5]};
@@ -147,6 +148,7 @@ static int contract_f32(const double *a, const orc_camera *cam, int tiles_x,
     float tx = fmaf(W[0], mux, fmaf(W[1], muy, fmaf(W[2], muz, cam->t[0])));
     float ty = fmaf(W[3], mux, fmaf(W[4], muy, fmaf(W[5], muz, cam->t[1])));
     float tz = fmaf(W[6], mux, fmaf(W[7], muy, fmaf(W[8], muz, cam->t[2])));
+    *depth = tz;
     if (!(tz > cam->znear)) return 0;
 
     /* EWA Jacobian with the frustum clamp */
@@ -249,7 +251,7 @@ int orc_preprocess(int64_t n, const double *attrs, const orc_camera *cam,
         orc_gauss *g = out + i;
         memset(g, 0, sizeof *g);
         g->visible = contract_f32(a, cam, tiles_x, tiles_y, g->rect, g->m32,
-                                  g->l32);
+                                  g->l32, &g->tz32);
 
         const double mu[3] = {a[0], a[1], a[2]};
         const double s[3] = {a[3], a[4], a[5]};
@@ -463,4 +465,65 @@ int64_t orc_pairs(const orc_gauss *g, const int64_t *offsets, const int32_t *gid
                 }
     }
     return k;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Comparator: sorted front-to-back alpha blending (App. B, Eq. 11)            */
+/* ------------------------------------------------------------------------- */
+
+static const orc_gauss *g_sort_base;
+
+static int by_depth(const void *x, const void *y)
+{
+    const int32_t i = *(const int32_t *)x, j = *(const int32_t *)y;
+    const float di = g_sort_base[i].tz32, dj = g_sort_base[j].tz32;
+    if (di < dj) return -1;
+    if (di > dj) return 1;
+    return (i > j) - (i < j);
+}
+
+int orc_rasterize_sorted(int64_t n, const orc_gauss *g, const int64_t *offsets,
+                         const int32_t *gids, int width, int height,
+                         const double bg[3], int tile_begin, int tile_end,
+                         double *out_rgb, int32_t *out_count)
+{
+    (void)n;
+    const int tiles_x = (width + ORC_TILE - 1) / ORC_TILE;
+    int64_t maxlen = 1;
+    for (int t = tile_begin; t < tile_end; ++t)
+        if (offsets[t + 1] - offsets[t] > maxlen) maxlen = offsets[t + 1] - offsets[t];
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)maxlen);
+    if (!list) return -1;
+    g_sort_base = g;
+    for (int t = tile_begin; t < tile_end; ++t) {
+        const int tx = t % tiles_x, ty = t / tiles_x;
+        for (int py = ty * ORC_TILE; py < (ty + 1) * ORC_TILE && py < height; ++py)
+            for (int px = tx * ORC_TILE; px < (tx + 1) * ORC_TILE && px < width; ++px) {
+                int64_t m = 0;
+                for (int64_t k = offsets[t]; k < offsets[t + 1]; ++k)
+                    if (orc_includes(g + gids[k], px, py)) list[m++] = gids[k];
+                qsort(list, (size_t)m, sizeof(int32_t), by_depth);
+                double C[3] = {0.0, 0.0, 0.0}, T = 1.0;
+                int32_t cnt = 0;
+                for (int64_t k = 0; k < m; ++k) {
+                    const orc_gauss *gi = g + list[k];
+                    double dx = px + 0.5 - gi->mean[0];
+                    double dy = py + 0.5 - gi->mean[1];
+                    double q = gi->conic[0] * dx * dx + 2.0 * gi->conic[1] * dx * dy +
+                               gi->conic[2] * dy * dy;
+                    double alpha = gi->opacity * exp(-0.5 * q);
+                    if (alpha > 0.99) alpha = 0.99;
+                    double next = T * (1.0 - alpha);
+                    if (next < 1e-4) break;
+                    for (int ch = 0; ch < 3; ++ch) C[ch] += gi->rgb[ch] * alpha * T;
+                    T = next;
+                    cnt += 1;
+                }
+                const int64_t p = (int64_t)py * width + px;
+                for (int ch = 0; ch < 3; ++ch) out_rgb[3 * p + ch] = C[ch] + T * bg[ch];
+                if (out_count) out_count[p] = cnt;
+            }
+    }
+    free(list);
+    return 0;
 }

@@ -63,6 +63,8 @@ typedef struct {
     float   m32[2];     /* FP32 contract pixel mean */
     float   l32[3];     /* FP32 contract factors: q = (l11 dx + l21 dy)^2
                            + (l22 dy)^2 */
+    float   tz32;       /* FP32 contract view depth (orders the sorted
+                           comparator) */
     double  mean[2];    /* FP64 pixel mean */
     double  cov[3];     /* FP64 Sigma_2D (a, b, c), dilation included */
     double  conic[3];   /* FP64 inverse of Sigma_2D (A, B, C) */
@@ -109,6 +111,18 @@ int orc_rasterize(int64_t n, const orc_gauss *g, const int64_t *offsets,
                   const int32_t *gids, int width, int height,
                   const double bg[3], int tile_begin, int tile_end,
                   double *out_rgb, double *out_aux, int32_t *out_count);
+
+/* Sorted front-to-back alpha blending (App. B, Eq. 11: C = sum c_i a_i T_i,
+ * T_i = prod_{j<i} (1 - a_j)), the 3DGS compositing the paper replaces; kept
+ * as the comparator of the sort-free renderer.  Per pixel the included
+ * Gaussians are ordered by FP32-contract view depth (ties by index); blending
+ * stops before the Gaussian that would bring T below 1e-4 (3DGS early
+ * termination); C += T c_bg at the end.  out_count (optional): Gaussians
+ * blended per pixel. */
+int orc_rasterize_sorted(int64_t n, const orc_gauss *g, const int64_t *offsets,
+                         const int32_t *gids, int width, int height,
+                         const double bg[3], int tile_begin, int tile_end,
+                         double *out_rgb, int32_t *out_count);
 
 /* All included (pixel, Gaussian) pairs: pixel index py * width + px and
  * Gaussian index, tile by tile, pixel by pixel, list order.  Returns the

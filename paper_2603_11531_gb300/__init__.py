@@ -30,6 +30,7 @@ MGS_ERR_NOT_READY = 7
 MGS_PREC_FP32 = 0
 MGS_PREC_FP16 = 1
 MGS_FLAG_NO_CULL = 1
+MGS_FLAG_SORTED = 2
 
 # Every entry point declared in include/mobilegs.h.
 EXPORTS = (

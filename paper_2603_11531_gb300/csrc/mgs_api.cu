@@ -99,6 +99,8 @@ struct mgs_workspace_s {
     int64_t bwd_g_cap = 0;
     float *bwd_partials = nullptr; // backward: per-CTA MLP weight gradients
     int64_t bwd_partials_cap = 0;
+    SortedScratch ss{};            // sorted comparator scratch
+    int64_t ss_n_cap = 0, ss_pairs_cap = 0;
     DevStatus *status = nullptr;
     int64_t last_tiles = 0;
     uint64_t grow_hint = 0;  // pairs needed by an overflowed render
@@ -270,6 +272,34 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     if ((e = launch_binning(a, w->ctx->sm_count, w->bases, stream)) != cudaSuccess)
         return cuda_fail(e, "binning launch");
     if (w->timing) cudaEventRecord(ev[2], stream);
+    if (opts->flags & MGS_FLAG_SORTED) {
+        if (out_aux) return fail(MGS_ERR_INVALID_ARG, "the sorted comparator has no aux output");
+        const int64_t nc = s->n > 0 ? s->n : 1;
+        const int64_t pc = (int64_t)w->pair_cap;
+        if (nc > w->ss_n_cap || pc > w->ss_pairs_cap) {
+            SortedScratch &q = w->ss;
+            dev_free(q.nkeys); dev_free(q.nkeys_tmp); dev_free(q.nvals); dev_free(q.nvals_tmp);
+            dev_free(q.rank); dev_free(q.keys); dev_free(q.keys_tmp); dev_free(q.vals);
+            dev_free(q.vals_tmp); dev_free(q.hist);
+            w->ss_n_cap = w->ss_pairs_cap = 0;
+            const int64_t hn = sorted_hist_entries(nc > pc ? nc : pc);
+            if ((e = dev_alloc(&q.nkeys, nc)) != cudaSuccess || (e = dev_alloc(&q.nkeys_tmp, nc)) != cudaSuccess ||
+                (e = dev_alloc(&q.nvals, nc)) != cudaSuccess || (e = dev_alloc(&q.nvals_tmp, nc)) != cudaSuccess ||
+                (e = dev_alloc(&q.rank, nc)) != cudaSuccess || (e = dev_alloc(&q.keys, pc)) != cudaSuccess ||
+                (e = dev_alloc(&q.keys_tmp, pc)) != cudaSuccess || (e = dev_alloc(&q.vals, pc)) != cudaSuccess ||
+                (e = dev_alloc(&q.vals_tmp, pc)) != cudaSuccess || (e = dev_alloc(&q.hist, hn)) != cudaSuccess)
+                return cuda_fail(e, "sorted scratch");
+            w->ss_n_cap = nc;
+            w->ss_pairs_cap = pc;
+        }
+        if ((e = launch_sorted(a, w->ss, stream)) != cudaSuccess) return cuda_fail(e, "sorted launch");
+        if (w->timing) {
+            cudaEventRecord(ev[3], stream);
+            w->pending.push_back(ev);
+        }
+        w->last_tiles = T;
+        return MGS_OK;
+    }
     if (prep) {
         *prep = a;
         w->last_tiles = T;
@@ -479,6 +509,16 @@ mgs_status mgs_workspace_destroy(mgs_workspace w) {
     dev_free(w->img);
     dev_free(w->bwd_g);
     dev_free(w->bwd_partials);
+    dev_free(w->ss.nkeys);
+    dev_free(w->ss.nkeys_tmp);
+    dev_free(w->ss.nvals);
+    dev_free(w->ss.nvals_tmp);
+    dev_free(w->ss.rank);
+    dev_free(w->ss.keys);
+    dev_free(w->ss.keys_tmp);
+    dev_free(w->ss.vals);
+    dev_free(w->ss.vals_tmp);
+    dev_free(w->ss.hist);
     dev_free(w->status);
     for (auto &q : w->pending)
         for (auto x : q) cudaEventDestroy(x);

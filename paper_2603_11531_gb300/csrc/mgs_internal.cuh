@@ -51,7 +51,7 @@ struct DevStatus {
 // rasteriser:
 //   a = (m_x, m_y, l11, l21)          FP32-contract mean and factors
 //   b = (l22, log2 o, -w, -w c_r)
-//   c = (-w c_g, -w c_b, 0, 0)
+//   c = (-w c_g, -w c_b, view depth (FP32 contract), 0)
 // The inclusion test is q = (l11 dx + l21 dy)^2 + (l22 dy)^2 <= 9 with
 // dx = x + 0.5 - m_x, dy = y + 0.5 - m_y, evaluated exactly as
 // e1 = fma(l11, dx, l21*dy), e2 = l22*dy, q = fma(e1, e1, e2*e2).
@@ -100,6 +100,19 @@ __device__ __forceinline__ bool block_may_hit(float mx, float my, float l11, flo
     const float m2 = 3.814697265625e-06f * (fabsf(l22) * (fabsf(dyb) + hy) + 4.0f);
     return (e1c - h1 <= 3.0f + m1) && (e2c - h2 <= 3.0f + m2);
 }
+
+// Scratch of the sorted comparator (mgs_sorted.cu).
+struct SortedScratch {
+    uint64_t *nkeys, *nkeys_tmp;   // [n]   depth ranking
+    uint32_t *nvals, *nvals_tmp;   // [n]
+    uint32_t *rank;                // [n]
+    uint64_t *keys, *keys_tmp;     // [capacity] (tile, rank) keys
+    uint32_t *vals, *vals_tmp;     // [capacity]
+    uint32_t *hist;                // [sorted_hist_entries(max(n, capacity))]
+};
+int64_t sorted_hist_entries(int64_t n_max);
+// Depth-sorts every tile list and blends front to back (Eq. 11 comparator).
+cudaError_t launch_sorted(const RenderArgs &a, const SortedScratch &s, cudaStream_t stream);
 
 // Launchers (each enqueues its kernels on `stream`).
 cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream);

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kThreads)
         ProjRec r;
         r.a = make_float4(c.mx, c.my, c.l11, c.l21);
         r.b = make_float4(c.l22, __log2f(opa), -w, -w * rgb[0]);
-        r.c = make_float4(-w * rgb[1], -w * rgb[2], 0.f, 0.f);
+        r.c = make_float4(-w * rgb[1], -w * rgb[2], c.tz, 0.f);
         args.rec[i] = r;
         args.rect[i] = make_uint2((unsigned)c.rect[0] | ((unsigned)c.rect[2] << 16),
                                   (unsigned)c.rect[1] | ((unsigned)c.rect[3] << 16));
