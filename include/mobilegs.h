@@ -25,8 +25,9 @@
  *     Scenes and workspaces own their device memory until destroyed.
  *   - Rendering calls are asynchronous on the given stream (NULL = the legacy
  *     default stream).  Arguments are checked on the host before any launch.
- *     Errors that only the device can see (tile-list capacity overflow) are
- *     recorded in the workspace and reported by mgs_workspace_sync().
+ *     Errors that only the device can see (tile-list capacity overflow, a
+ *     tensor-core wait that ran out) are recorded in the workspace and
+ *     reported by mgs_workspace_sync().
  *   - A workspace holds the per-frame scratch (projected Gaussians, tile
  *     lists).  Renders that share a workspace must be ordered on one stream;
  *     concurrent renders need one workspace each.
@@ -63,6 +64,8 @@ enum { MGS_PREC_FP32 = 0, MGS_PREC_FP16 = 1 };
 enum {
     MGS_FLAG_NO_CULL = 1u, /* debug: skip the conservative per-warp culling of
                               tile lists (the image must not change) */
+    MGS_FLAG_MLP_MMA_SYNC = 4u, /* run the MLP on warp-level mma.sync instead
+                              of tcgen05 (comparison and testing) */
     MGS_FLAG_SORTED = 2u   /* comparator, not the paper's method: depth-sort
                               every tile list (radix sort) and alpha-blend
                               front to back, C = sum c_i a_i T_i + T c_bg
@@ -148,8 +151,10 @@ mgs_status mgs_workspace_reserve(mgs_workspace ws, int64_t n, int32_t width,
 int64_t mgs_workspace_bytes(mgs_workspace ws);
 /* Wait for `stream`, then report renders since the previous sync:
  * MGS_ERR_OVERFLOW if any ran out of tile-list capacity (the workspace is then
- * grown so that a repeat succeeds).  *pairs_out (nullable) = the largest
- * number of (tile, Gaussian) pairs any of them needed. */
+ * grown so that a repeat succeeds); MGS_ERR_TIMEOUT if a tensor-core MMA wait
+ * in the MLP gave up (that image is invalid; checked first).  *pairs_out
+ * (nullable) = the largest number of (tile, Gaussian) pairs any of them
+ * needed. */
 mgs_status mgs_workspace_sync(mgs_workspace ws, mgs_stream stream,
                               int64_t *pairs_out);
 

@@ -31,6 +31,7 @@ MGS_PREC_FP32 = 0
 MGS_PREC_FP16 = 1
 MGS_FLAG_NO_CULL = 1
 MGS_FLAG_SORTED = 2
+MGS_FLAG_MLP_MMA_SYNC = 4
 
 # Every entry point declared in include/mobilegs.h.
 EXPORTS = (

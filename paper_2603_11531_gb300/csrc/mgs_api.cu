@@ -553,7 +553,9 @@ mgs_status mgs_workspace_sync(mgs_workspace w, mgs_stream stream_, int64_t *pair
     if ((e = cudaMemset(w->status, 0, offsetof(DevStatus, last_pairs))) != cudaSuccess)
         return cuda_fail(e, "status reset");
     if (pairs_out) *pairs_out = (int64_t)h.max_pairs;
-    if (h.overflow) {
+    if (h.overflow & kStatusMmaTimeout)
+        return fail(MGS_ERR_TIMEOUT, "a tensor-core MMA wait in preprocessing timed out");
+    if (h.overflow & kStatusOverflow) {
         uint64_t need = h.max_pairs + h.max_pairs / 4 + 1024;
         if (w->grow_hint < need) w->grow_hint = need;
         return fail(MGS_ERR_OVERFLOW, "tile lists needed %llu pairs, capacity was %llu",

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
         offsets[T] = (uint32_t)K;
         status->last_pairs = K;
         atomicMax(&status->max_pairs, K);
-        if (K > capacity || K > 0xFFFFFFFFull) atomicOr(&status->overflow, 1u);
+        if (K > capacity || K > 0xFFFFFFFFull) atomicOr(&status->overflow, kStatusOverflow);
     }
 }
 

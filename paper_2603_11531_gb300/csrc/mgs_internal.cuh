@@ -40,8 +40,10 @@ struct DevMLP {
 };
 
 // Device-visible status of a workspace (accumulates until the host syncs).
+constexpr unsigned kStatusOverflow = 1u;    // some render exceeded its pair capacity
+constexpr unsigned kStatusMmaTimeout = 2u;  // a tcgen05 MMA wait ran out (results invalid)
 struct DevStatus {
-    unsigned int overflow;          // nonzero: some render exceeded capacity
+    unsigned int overflow;          // kStatus* bits seen since the last sync
     unsigned int pad;
     unsigned long long max_pairs;   // largest pair count seen since the last sync
     unsigned long long last_pairs;  // pair count of the most recent render

@@ -13,6 +13,7 @@
 // bits.  Colour, MLP and weight are ordinary FP32 values.
 #include "mgs_internal.cuh"
 #include "mgs_mlp.cuh"
+#include "mgs_tcgen05.cuh"
 
 namespace mgs {
 namespace {
@@ -172,14 +173,22 @@ __device__ __forceinline__ void camera_centre(const DevCamera &cam, float (&c)[3
         c[j] = -(cam.R[j] * cam.t[0] + cam.R[3 + j] * cam.t[1] + cam.R[6 + j] * cam.t[2]);
 }
 
-template <bool kFP16, bool kMLP, bool kResidual>
-__global__ void __launch_bounds__(kThreads)
+// kTC: the MLP runs on tcgen05 (TMEM accumulators, one CTA = 128 rows);
+// otherwise on mma.sync (one warp = 32 rows).
+template <bool kFP16, bool kMLP, bool kResidual, bool kTC>
+__global__ void __launch_bounds__(kTC ? tc::kThreads : kThreads)
     k_preprocess(RenderArgs args) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kStep = kTC ? tc::kThreads : kThreads;   // Gaussians per CTA step
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpSmem &sm = *reinterpret_cast<MlpSmem *>(smem_raw);
+    tc::Smem &tsm = *reinterpret_cast<tc::Smem *>(smem_raw);
     const DevCamera &cam = args.cam;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if constexpr (kMLP) {
+    uint32_t tc_phase = 0;
+    bool tc_ok = true;
+    if constexpr (kMLP && kTC) {
+        tc::setup(tsm, args.mlp);
+    } else if constexpr (kMLP) {
         mlp_load_weights(sm, args.mlp);
         __syncthreads();
     }
@@ -187,8 +196,8 @@ __global__ void __launch_bounds__(kThreads)
     camera_centre(cam, cc);
     const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f;
 
-    for (int64_t base = (int64_t)blockIdx.x * kThreads; base < args.n;
-         base += (int64_t)gridDim.x * kThreads) {
+    for (int64_t base = (int64_t)blockIdx.x * kStep; base < args.n;
+         base += (int64_t)gridDim.x * kStep) {
         const int64_t i = base + threadIdx.x;
         const bool valid = i < args.n;
         float v[kRec];
@@ -206,8 +215,7 @@ __global__ void __launch_bounds__(kThreads)
         }
         float phi = 1.0f, opa = 0.f, dres[3] = {0.f, 0.f, 0.f};
         if constexpr (kMLP) {
-            // feature row [P, s, q_hat, Y] -> BF16 in shared memory (row = lane)
-            __nv_bfloat16 *xr = &sm.x[warp][lane * kXStride];
+            // feature row [P, s, q_hat, Y]
             float f[kMlpK1];
 #pragma unroll
             for (int k = 0; k < kMlpK1; ++k) f[k] = 0.f;
@@ -218,25 +226,34 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
                 for (int k = 0; k < 12; ++k) f[10 + k] = v[11 + k];
             }
+            float o[5];
+            if constexpr (kTC) {
+                tc::put_features(tsm, f);
+                tc_ok &= tc::mlp_cta(tsm, tc_phase, o);
+            } else {
+                // BF16 row in shared memory (row = lane), one warp per 32 rows
+                __nv_bfloat16 *xr = &sm.x[warp][lane * kXStride];
 #pragma unroll
-            for (int k = 0; k < kMlpK1; k += 8) {
-                uint4 u;
-                u.x = pack_bf16(f[k], f[k + 1]);
-                u.y = pack_bf16(f[k + 2], f[k + 3]);
-                u.z = pack_bf16(f[k + 4], f[k + 5]);
-                u.w = pack_bf16(f[k + 6], f[k + 7]);
-                *reinterpret_cast<uint4 *>(xr + k) = u;
+                for (int k = 0; k < kMlpK1; k += 8) {
+                    uint4 u;
+                    u.x = pack_bf16(f[k], f[k + 1]);
+                    u.y = pack_bf16(f[k + 2], f[k + 3]);
+                    u.z = pack_bf16(f[k + 4], f[k + 5]);
+                    u.w = pack_bf16(f[k + 6], f[k + 7]);
+                    *reinterpret_cast<uint4 *>(xr + k) = u;
+                }
+                __syncwarp();
+                mlp_warp<false>(sm, warp, lane, nullptr, nullptr);
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < 5; ++k) o[k] = sm.out[warp][lane][k];
+                __syncwarp();
             }
-            __syncwarp();
-            mlp_warp<false>(sm, warp, lane, nullptr, nullptr);
-            __syncwarp();
-            const float *o = sm.out[warp][lane];
             phi = fmaxf(o[0], 0.f);
             opa = 1.0f / (1.0f + __expf(-o[1]));
             dres[0] = o[2];
             dres[1] = o[3];
             dres[2] = o[4];
-            __syncwarp();
         }
         if (!valid) continue;
         if constexpr (!kMLP) opa = v[10];
@@ -268,22 +285,29 @@ __global__ void __launch_bounds__(kThreads)
         args.rect[i] = make_uint2((unsigned)c.rect[0] | ((unsigned)c.rect[2] << 16),
                                   (unsigned)c.rect[1] | ((unsigned)c.rect[3] << 16));
     }
+    if constexpr (kMLP && kTC) {
+        tc::teardown(tsm);
+        if (!tc_ok && threadIdx.x == 0) atomicOr(&args.status->overflow, kStatusMmaTimeout);
+    }
 }
 
-template <bool kFP16, bool kMLP, bool kResidual>
+template <bool kFP16, bool kMLP, bool kResidual, bool kTC>
 cudaError_t launch_t(const RenderArgs &a, int sm_count, cudaStream_t stream) {
-    const size_t smem = kMLP ? sizeof(MlpSmem) : 16;
-    auto kern = k_preprocess<kFP16, kMLP, kResidual>;
+    const size_t smem = kMLP ? (kTC ? sizeof(tc::Smem) : sizeof(MlpSmem)) : 16;
+    auto kern = k_preprocess<kFP16, kMLP, kResidual, kTC>;
     if (kMLP) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    int64_t blocks = (a.n + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)sm_count * 8;
+    const int threads = (kMLP && kTC) ? tc::kThreads : kThreads;
+    int64_t blocks = (a.n + threads - 1) / threads;
+    // tcgen05: at most 3 CTAs per SM (shared memory; 3 x 128 of the SM's 512
+    // TMEM columns)
+    const int64_t cap = (int64_t)sm_count * ((kMLP && kTC) ? 3 : 8);
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, kThreads, smem, stream>>>(a);
+    kern<<<(unsigned)blocks, threads, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -291,15 +315,23 @@ cudaError_t launch_t(const RenderArgs &a, int sm_count, cudaStream_t stream) {
 
 cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream) {
     const bool fp16 = a.precision == MGS_PREC_FP16;
+    const bool sync_mma = (a.flags & MGS_FLAG_MLP_MMA_SYNC) != 0;
     if (a.use_mlp) {
+        if (sync_mma) {
+            if (a.rgb_residual)
+                return fp16 ? launch_t<true, true, true, false>(a, sm_count, stream)
+                            : launch_t<false, true, true, false>(a, sm_count, stream);
+            return fp16 ? launch_t<true, true, false, false>(a, sm_count, stream)
+                        : launch_t<false, true, false, false>(a, sm_count, stream);
+        }
         if (a.rgb_residual)
-            return fp16 ? launch_t<true, true, true>(a, sm_count, stream)
-                        : launch_t<false, true, true>(a, sm_count, stream);
-        return fp16 ? launch_t<true, true, false>(a, sm_count, stream)
-                    : launch_t<false, true, false>(a, sm_count, stream);
+            return fp16 ? launch_t<true, true, true, true>(a, sm_count, stream)
+                        : launch_t<false, true, true, true>(a, sm_count, stream);
+        return fp16 ? launch_t<true, true, false, true>(a, sm_count, stream)
+                    : launch_t<false, true, false, true>(a, sm_count, stream);
     }
-    return fp16 ? launch_t<true, false, false>(a, sm_count, stream)
-                : launch_t<false, false, false>(a, sm_count, stream);
+    return fp16 ? launch_t<true, false, false, false>(a, sm_count, stream)
+                : launch_t<false, false, false, false>(a, sm_count, stream);
 }
 
 }  // namespace mgs

@@ -181,11 +181,13 @@ void mgs_server_s::run() {
                 Request &rq = reqs[sl.ticket];
                 const uint64_t need = sl.status_host->last_pairs;
                 pairs_cache[cache_key(rq.scene, rq.cam.width, rq.cam.height)] = need;
-                if (q != cudaSuccess) {
-                    rq.result = MGS_ERR_CUDA;
+                if (q != cudaSuccess || (sl.status_host->overflow & kStatusMmaTimeout)) {
+                    rq.result = q != cudaSuccess ? MGS_ERR_CUDA : MGS_ERR_TIMEOUT;
                     rq.state = kDone;
                     rq.t_done = t;
                     ++completed;
+                    if (q == cudaSuccess)  // clear the sticky flag for the slot's next request
+                        cudaMemsetAsync(sl.args.status, 0, sizeof(unsigned int), sl.stream);
                 } else if (need > sl.args.capacity && rq.attempts < 3) {
                     rq.pairs_hint = need + need / 4 + 1024;  // retry with room
                     rq.state = kQueued;

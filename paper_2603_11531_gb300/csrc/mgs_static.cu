@@ -150,6 +150,8 @@ extern "C" mgs_status mgs_render_static(const void *attrs, int64_t n, int32_t pr
         snprintf(msg, sizeof msg, "CUDA error: %s", cudaGetErrorString(e));
         return fail_static(MGS_ERR_CUDA, msg);
     }
+    if (h.overflow & kStatusMmaTimeout)
+        return fail_static(MGS_ERR_TIMEOUT, "a tensor-core MMA wait in preprocessing timed out");
     if (h.last_pairs > (unsigned long long)kMaxPairs) {
         snprintf(msg, sizeof msg,
                  "view needs %llu (tile, Gaussian) pairs; the allocation-free limit is %lld",

@@ -1,0 +1,261 @@
+// Eq. 4 MLP on the 5th-generation tensor cores (tcgen05, sm_100-family):
+// one CTA of 256 threads evaluates 256 Gaussians per step as two M = 128
+// tiles that share one copy of the weights.
+//
+//   operands   shared memory, canonical no-swizzle K-major layout: 8-row x
+//              16-byte core matrices stored contiguously (128 B each), core
+//              matrices adjacent in K 128 B apart (leading byte offset),
+//              adjacent in M/N (K/8) x 128 B apart (stride byte offset);
+//   issue      one thread issues tcgen05.mma (kind::f16, BF16 inputs, FP32
+//              accumulate) for each K = 16 step and commits to an mbarrier;
+//   result     accumulators live in TMEM (128 columns per CTA: tile 0 in
+//              columns 0-63, tile 1 in 64-127, layer 2 reusing layer 1's
+//              columns once they are read); thread t reads row t % 128 of tile
+//              t / 128 with tcgen05.ld.32x32b (warp w sees lanes 32 (w % 4)..);
+//   head       the 64 -> 5 head (BF16 h2, FP32 accumulate) runs on the CUDA
+//              cores from the thread's own row, saving a third round trip.
+//
+// Every wait on the mbarrier is bounded; on timeout the kernel records an
+// error flag in the workspace status and carries on (the host reports
+// MGS_ERR_TIMEOUT at the next sync).
+#pragma once
+
+#include "mgs_internal.cuh"
+
+namespace mgs {
+namespace tc {
+
+constexpr int kRows = 128;          // rows per MMA tile
+constexpr int kTiles = 2;           // tiles per CTA step
+constexpr int kThreads = kRows * kTiles;
+constexpr int kTmemCols = 128;
+constexpr unsigned kWaitLimit = 1u << 22;
+
+// byte offset of element (row, k) in a K-major canonical tile with K columns
+__device__ __forceinline__ uint32_t core_off(int row, int k, int K) {
+    return (uint32_t)((((row >> 3) * (K >> 3) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                // base offset 0, no swizzle
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     mbar)
+                 : "memory");
+}
+
+// Bounded wait for the mbarrier phase; returns false on timeout.
+__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t phase) {
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared memory of the tcgen05 MLP (operands in canonical layout).
+struct Smem {
+    alignas(128) __nv_bfloat16 x[kTiles][kRows * kMlpK1];       // A of layer 1, K = 32
+    alignas(128) __nv_bfloat16 h1[kTiles][kRows * kMlpHidden];  // A of layer 2, K = 64
+    alignas(128) __nv_bfloat16 w1[kMlpHidden * kMlpK1];         // B, N = 64, K = 32
+    alignas(128) __nv_bfloat16 w2[kMlpHidden * kMlpHidden];     // B, N = 64, K = 64
+    float w3[kMlpOut][kMlpHidden];                               // head (BF16 values)
+    float b1[kMlpHidden], b2[kMlpHidden], b3[kMlpOut];
+    alignas(8) unsigned long long mbar;
+    uint32_t tmem_base;
+};
+
+// two BF16 values at (row, k), (row, k + 1), k even: one 4-byte store
+__device__ __forceinline__ void store_bf16x2(__nv_bfloat16 *base, uint32_t off, float lo,
+                                             float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<unsigned char *>(base) + off) = h;
+}
+
+// Loads the packed weights into canonical layout, initialises the mbarrier
+// and allocates TMEM.  All threads of the CTA must call it.
+__device__ __forceinline__ void setup(Smem &sm, const DevMLP &mlp) {
+    for (int e = threadIdx.x; e < kMlpHidden * kMlpK1; e += blockDim.x) {
+        const int n = e / kMlpK1, k = e % kMlpK1;
+        *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(sm.w1) +
+                                           core_off(n, k, kMlpK1)) = mlp.w1[e];
+    }
+    for (int e = threadIdx.x; e < kMlpHidden * kMlpHidden; e += blockDim.x) {
+        const int n = e / kMlpHidden, k = e % kMlpHidden;
+        *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(sm.w2) +
+                                           core_off(n, k, kMlpHidden)) = mlp.w2[e];
+    }
+    for (int e = threadIdx.x; e < kMlpOut * kMlpHidden; e += blockDim.x)
+        sm.w3[e / kMlpHidden][e % kMlpHidden] = __bfloat162float(mlp.w3[e]);
+    for (int e = threadIdx.x; e < kMlpHidden; e += blockDim.x) {
+        sm.b1[e] = mlp.b1[e];
+        sm.b2[e] = mlp.b2[e];
+    }
+    if (threadIdx.x < kMlpOut) sm.b3[threadIdx.x] = mlp.b3[threadIdx.x];
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&sm.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(&sm.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+}
+
+__device__ __forceinline__ void teardown(Smem &sm) {
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem_base),
+                     "r"(kTmemCols)
+                     : "memory");
+}
+
+// Issues one layer (all K steps, both tiles) from thread 0 and waits for it.
+// Tile t reads A at a_t and writes TMEM columns 64 t .. 64 t + 63.
+__device__ __forceinline__ bool layer(Smem &sm, const void *a0, const void *a1, const void *b,
+                                      int K, uint32_t &phase) {
+    if (threadIdx.x == 0) {
+        fence_after();
+        const uint32_t sbo = (uint32_t)(K >> 3) << 7;
+        const uint32_t idesc = idesc_bf16(kRows, kMlpHidden);
+        const void *as[2] = {a0, a1};
+#pragma unroll
+        for (int t = 0; t < kTiles; ++t) {
+#pragma unroll 1
+            for (int s = 0; s < K / 16; ++s) {
+                const uint64_t ad = smem_desc(saddr(as[t]) + (uint32_t)s * 256u, 128u, sbo);
+                const uint64_t bd = smem_desc(saddr(b) + (uint32_t)s * 256u, 128u, sbo);
+                mma(sm.tmem_base + 64u * (uint32_t)t, ad, bd, idesc, s > 0 ? 1u : 0u);
+            }
+        }
+        commit(saddr(&sm.mbar));
+    }
+    const bool ok = wait(saddr(&sm.mbar), phase);
+    phase ^= 1u;
+    fence_after();
+    return ok;
+}
+
+// Writes this thread's 32 features (tile threadIdx.x / 128, row
+// threadIdx.x % 128) into the layer-1 operand as BF16.
+__device__ __forceinline__ void put_features(Smem &sm, const float (&f)[kMlpK1]) {
+    const int tile = threadIdx.x / kRows, row = threadIdx.x % kRows;
+#pragma unroll
+    for (int k = 0; k < kMlpK1; k += 2)
+        store_bf16x2(sm.x[tile], core_off(row, k, kMlpK1), f[k], f[k + 1]);
+}
+
+// The MLP of the CTA's 256 rows: each thread has already written its row's
+// 32 BF16 features into sm.x (put_features); out receives (phi-logit,
+// o-logit, d_r, d_g, d_b) of its own row, biases added.  All threads call it.
+__device__ __forceinline__ bool mlp_cta(Smem &sm, uint32_t &phase, float (&out)[5]) {
+    const int tile = threadIdx.x / kRows, row = threadIdx.x % kRows;
+    const int quad = (threadIdx.x >> 5) & 3;   // TMEM lane quadrant of this warp
+    const uint32_t col0 = sm.tmem_base + 64u * (uint32_t)tile + ((uint32_t)(32 * quad) << 16);
+    bool ok = true;
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    // layer 1: [128 x 32] x [32 x 64] per tile
+    ok &= layer(sm, sm.x[0], sm.x[1], sm.w1, kMlpK1, phase);
+#pragma unroll
+    for (int c = 0; c < kMlpHidden; c += 16) {
+        float v[16];
+        ld16(col0 + (uint32_t)c, v);
+#pragma unroll
+        for (int i = 0; i < 16; i += 2)
+            store_bf16x2(sm.h1[tile], core_off(row, c + i, kMlpHidden),
+                         fmaxf(v[i] + sm.b1[c + i], 0.0f), fmaxf(v[i + 1] + sm.b1[c + i + 1], 0.0f));
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    // layer 2: [128 x 64] x [64 x 64] per tile, into the same TMEM columns
+    ok &= layer(sm, sm.h1[0], sm.h1[1], sm.w2, kMlpHidden, phase);
+    float acc[kMlpOut];
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) acc[k] = sm.b3[k];
+#pragma unroll
+    for (int c = 0; c < kMlpHidden; c += 16) {
+        float v[16];
+        ld16(col0 + (uint32_t)c, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            // h2 = BF16(ReLU(.)), the same rounding the head MMA would see
+            const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(v[i] + sm.b2[c + i], 0.0f)));
+#pragma unroll
+            for (int k = 0; k < kMlpOut; ++k) acc[k] = fmaf(sm.w3[k][c + i], h, acc[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) out[k] = acc[k];
+    fence_before();
+    __syncthreads();
+    return ok;
+}
+
+}  // namespace tc
+}  // namespace mgs
