@@ -117,6 +117,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of `values` over all ranks (identity with one
+    rank): the slowest rank's time is the job's time."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the slowest
+    rank's time (weak scaling: every rank renders its own fixed share)."""
+    return units_per_rank * world / (max_ms / 1000.0)
+
+
 def cpu_baseline_sample(tile_stride: int = 8, pose: int = 0):
     """Time the FP64 oracle as it stands (single thread) on one pose of the
     workload: full preprocessing (600k Gaussians incl. MLP) and binning, and
@@ -241,13 +258,9 @@ def run_gpu(args):
     st, _ = m.mgs_workspace_sync(r.ws, stream, allow_overflow=True)
     if st != m.MGS_OK:
         raise RuntimeError("tile-list overflow inside the timed region")
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks([sum(step_ms)], dist, "cuda")[0]
     frames = N_POSES * args.steps * world
-    fps = frames / (total_ms / 1000.0)
+    fps = job_rate(N_POSES * args.steps, world, total_ms)
 
     stage_per_frame = [x / max(timed_frames, 1) for x in stage_ms]
     rast = {"ms_per_frame": stage_per_frame[2]}
@@ -264,12 +277,8 @@ def run_gpu(args):
         stream.synchronize()
         if i >= args.warmup:
             e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-    e2e_total = sum(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_fps = frames / (e2e_total / 1000.0)
+    e2e_total = max_over_ranks([sum(e2e_ms)], dist, "cuda")[0]
+    e2e_fps = job_rate(N_POSES * args.steps, world, e2e_total)
 
     peaks, peaks_kind = _peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
