@@ -288,7 +288,7 @@ def run_gpu(args):
     # (7 for the quadratic form, 9 for alpha and the A/B/T updates) + 1 MUFU
     achieved = 16.0 * mean_hits / (rast["ms_per_frame"] / 1000.0) / 1e12
     peak_alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
-    traffic = _profiled_traffic("k_raster_unbounded600k_1600x1063.md")
+    traffic = _profiled_traffic("k_raster_tc_unbounded600k_1600x1063.md")
 
     if rank == 0:
         line = {
@@ -305,7 +305,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_fps, "unit": "FPS",
                     "h2d_bytes_per_step": N_POSES * 68,
                     "d2h_bytes_per_step": N_POSES * H * W * 12},
-            "roofline": {"bound": "alu", "kernel": "k_raster",
+            "roofline": {"bound": "alu", "kernel": "k_raster_tc",
                          "achieved": achieved, "peak": peak_alu, "unit": "T FP32-lane-op/s",
                          "frac": achieved / peak_alu, "traffic": traffic,
                          "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median "

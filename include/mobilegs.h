@@ -66,6 +66,9 @@ enum {
                               tile lists (the image must not change) */
     MGS_FLAG_MLP_MMA_SYNC = 4u, /* run the MLP on warp-level mma.sync instead
                               of tcgen05 (comparison and testing) */
+    MGS_FLAG_RASTER_FMA = 8u, /* FP16 scenes: accumulate A and B on the FP32
+                              FMA pipe instead of the tensor cores (exact
+                              FP32 sums, slower; comparison and testing) */
     MGS_FLAG_SORTED = 2u   /* comparator, not the paper's method: depth-sort
                               every tile list (radix sort) and alpha-blend
                               front to back, C = sum c_i a_i T_i + T c_bg

@@ -32,6 +32,7 @@ MGS_PREC_FP16 = 1
 MGS_FLAG_NO_CULL = 1
 MGS_FLAG_SORTED = 2
 MGS_FLAG_MLP_MMA_SYNC = 4
+MGS_FLAG_RASTER_FMA = 8
 
 # Every entry point declared in include/mobilegs.h.
 EXPORTS = (

@@ -191,11 +191,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
 
 // Rasterisation order: tiles by decreasing list length (bucketed by
 // floor(log2(length))), so the longest tiles start first and the tail of the
-// launch is made of short tiles.  One block.
+// launch is made of short tiles.  One block.  Also hands this frame's weight
+// bound to the rasteriser and resets the accumulator for the next frame.
 __global__ void __launch_bounds__(kScanThreads) k_tile_order(const uint32_t *__restrict__ count,
-                                                             int T, uint32_t *__restrict__ order) {
+                                                             int T, uint32_t *__restrict__ order,
+                                                             DevStatus *status) {
     __shared__ uint32_t hist[33], start[33];
     const int tid = threadIdx.x;
+    if (tid == 0) {
+        status->wmax_frame_bits = status->wmax_bits;
+        status->wmax_bits = 0u;
+    }
     if (tid < 33) hist[tid] = 0u;
     __syncthreads();
     for (int t = tid; t < T; t += blockDim.x) {
@@ -248,7 +254,7 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases,
     }
     k_scan<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, T, a.capacity, a.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_tile_order<<<1, kScanThreads, 0, stream>>>(a.tile_count, T, a.tile_order);
+    k_tile_order<<<1, kScanThreads, 0, stream>>>(a.tile_count, T, a.tile_order, a.status);
     if ((e = cudaGetLastError()) != cudaSuccess || a.n == 0) return e;
     k_bin_scatter<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, a.tile_offsets,
                                                     bases, a.gids, a.capacity, a.status);

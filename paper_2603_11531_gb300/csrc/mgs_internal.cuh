@@ -47,6 +47,12 @@ struct DevStatus {
     unsigned int pad;
     unsigned long long max_pairs;   // largest pair count seen since the last sync
     unsigned long long last_pairs;  // pair count of the most recent render
+    // Largest |w c| and w over the visible Gaussians (FP32 bits; positive
+    // floats order as unsigned integers): accumulated by preprocessing,
+    // handed to the frame's rasteriser (wmax_frame_bits) and reset by
+    // k_tile_order, which runs between the two.
+    unsigned int wmax_bits;
+    unsigned int wmax_frame_bits;
 };
 
 // Projected Gaussian (48 bytes), written by preprocessing, read by the

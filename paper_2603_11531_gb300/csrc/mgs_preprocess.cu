@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(kTC ? tc::kThreads : kThreads)
     float cc[3];
     camera_centre(cam, cc);
     const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f;
+    float wbound = 0.0f;
 
     for (int64_t base = (int64_t)blockIdx.x * kStep; base < args.n;
          base += (int64_t)gridDim.x * kStep) {
@@ -284,7 +285,13 @@ __global__ void __launch_bounds__(kTC ? tc::kThreads : kThreads)
         args.rec[i] = r;
         args.rect[i] = make_uint2((unsigned)c.rect[0] | ((unsigned)c.rect[2] << 16),
                                   (unsigned)c.rect[1] | ((unsigned)c.rect[3] << 16));
+        wbound = fmaxf(wbound, w * fmaxf(fmaxf(1.0f, rgb[0]), fmaxf(rgb[1], rgb[2])));
     }
+    // bound on the rasteriser's weights |w|, |w c| for this frame
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wbound = fmaxf(wbound, __shfl_xor_sync(0xffffffffu, wbound, o));
+    if ((threadIdx.x & 31) == 0 && wbound > 0.0f)
+        atomicMax(&args.status->wmax_bits, __float_as_uint(wbound));
     if constexpr (kMLP && kTC) {
         tc::teardown(tsm);
         if (!tc_ok && threadIdx.x == 0) atomicOr(&args.status->overflow, kStatusMmaTimeout);

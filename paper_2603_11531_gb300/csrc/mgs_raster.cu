@@ -9,6 +9,13 @@
 // with a conservative bound and compacting (ballot) the candidates before
 // accumulating them in registers.  No atomics, no sort: every pixel is owned
 // by exactly one thread.
+//
+// FP16-attribute scenes take the sums A and B on the tensor cores instead
+// (raster_tile_tc below): alpha is still computed, tested and multiplied
+// into T in FP32 exactly as above, but a_i w_i c_i and a_i w_i are summed by
+// mma.sync (m16n8k16, FP16 operands, FP32 accumulation) with the weights split
+// into FP16 high and low parts, which leaves alpha's FP16 rounding (relative
+// 2^-12 per term) as the only extra error.
 #include "mgs_internal.cuh"
 
 namespace mgs {
@@ -197,6 +204,261 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
 }
 
 // One CTA per tile, longest tile lists first.
+// ---------------------------------------------------------------------------
+// Tensor-core accumulation of A and B (FP16-attribute scenes).
+//
+// One CTA (four warps) per tile; warp w owns the 16x4 block of rows
+// 4w..4w+3.  A warp's 64 pixels are the M = 64 rows of four m16n8k16 tiles:
+// lane (g, t) = (lane / 4, lane % 4) owns the eight pixels
+// x = 8 (g / 4) + 0..7 of row g % 4 (rows g and g + 8 of m-tile i are
+// pixels 2i and 2i + 1), shared by the four lanes of its quad.  Candidates
+// are gathered into chunks of 16 Gaussians (the K dimension); lane t of a
+// quad evaluates chunk entries 2t, 2t + 1, 2t + 8, 2t + 9 at its pixels, which
+// is exactly the A fragment it holds.  B = the chunk's weights
+// [-w c_r, -w c_g, -w c_b, -w] as FP16 high parts (columns 0-3) and low
+// parts (columns 4-7), so column c + column c + 4 is the sum with a 22-bit
+// weight.  Weights are scaled by a power of two when the frame's largest
+// weight would overflow FP16 (the scale cancels in A / B and is divided out).
+constexpr int kTcThreads = 128;
+constexpr int kTcWarps = kTcThreads / 32;
+constexpr int kRing = 48;        // candidate slots per warp: three chunks of 16
+
+struct TcSmem {
+    ulonglong2 geo[kTcWarps][3][kRing];   // duplicated pairs as in accumulate()
+    __half wt[kTcWarps][8][kRing];        // weight column c of slot s (FP16)
+};
+
+__device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                        uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Negated, clamped alpha of ring slot s at the lane's eight pixels (pairs of
+// pixels 2i, 2i + 1), the same FP32 sequence as accumulate(); T updated.
+template <bool kCount>
+__device__ __forceinline__ void tc_alpha(const ulonglong2 (*geo)[kRing], int s, const f2 (&pxc)[4],
+                                         f2 pyc, f2 kq2, f2 (&T)[4], f2 (&n)[4], int (&cnt)[8]) {
+    const ulonglong2 s0 = geo[0][s], s1 = geo[1][s], s2 = geo[2][s];
+    const f2 dy = sub2(pyc, s0.y);
+    const f2 ldy = mul2(s1.y, dy);
+    const f2 e2 = mul2(s2.x, dy);
+    const f2 e2s = mul2(e2, e2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const f2 dx = sub2(pxc[i], s0.x);
+        const f2 e1 = fma2(s1.x, dx, ldy);
+        const f2 q = fma2(e1, e1, e2s);
+        const f2 g = fma2(q, kq2, s2.y);
+        float q0, q1, g0, g1;
+        upk(q, q0, q1);
+        upk(g, g0, g1);
+        const float n0 = q0 <= 9.0f ? fmaxf(-ex2(g0), -0.99f) : 0.0f;
+        const float n1 = q1 <= 9.0f ? fmaxf(-ex2(g1), -0.99f) : 0.0f;
+        if (kCount) {
+            cnt[2 * i] += q0 <= 9.0f;
+            cnt[2 * i + 1] += q1 <= 9.0f;
+        }
+        n[i] = pk(n0, n1);
+        T[i] = fma2(n[i], T[i], T[i]);
+    }
+}
+
+// One chunk of 16 candidates starting at ring slot c0 (a multiple of 16).
+template <bool kCount>
+__device__ __forceinline__ void tc_chunk(const ulonglong2 (*geo)[kRing], const __half (*wt)[kRing],
+                                         int c0, int g, int t, const f2 (&pxc)[4], f2 pyc, f2 kq2,
+                                         f2 (&T)[4], float (&D)[4][4], int (&cnt)[8]) {
+    uint32_t a[4][4];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        f2 na[4], nb[4];
+        tc_alpha<kCount>(geo, c0 + 2 * t + 8 * p, pxc, pyc, kq2, T, na, cnt);
+        tc_alpha<kCount>(geo, c0 + 2 * t + 8 * p + 1, pxc, pyc, kq2, T, nb, cnt);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float a0, a1, b0, b1;
+            upk(na[i], a0, a1);
+            upk(nb[i], b0, b1);
+            a[i][2 * p] = h2bits(a0, b0);      // pixel 2i (row g): k = 2t (+8p), 2t + 1 (+8p)
+            a[i][2 * p + 1] = h2bits(a1, b1);  // pixel 2i + 1 (row g + 8)
+        }
+    }
+    const uint32_t *col = reinterpret_cast<const uint32_t *>(wt[g]);
+    const uint32_t b0 = col[(c0 >> 1) + t];      // k = 2t, 2t + 1 of column g
+    const uint32_t b1 = col[(c0 >> 1) + 4 + t];  // k = 2t + 8, 2t + 9
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mma_f16(D[i], a[i], b0, b1);
+}
+
+template <bool kAux, bool kCount>
+__device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile, TcSmem &sm) {
+    const DevCamera &cam = args.cam;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int bx0 = tx * kTile, by0 = ty * kTile + 4 * warp;
+    const int xb = bx0 + 8 * (g >> 2);
+    const int py = by0 + (g & 3);
+    const ulonglong2(*geo)[kRing] = sm.geo[warp];
+    __half(*wt)[kRing] = sm.wt[warp];
+
+    const uint32_t start = args.tile_offsets[tile];
+    const uint32_t end = args.tile_offsets[tile + 1];
+    const bool no_cull = (args.flags & MGS_FLAG_NO_CULL) != 0;
+    const float bcx = (float)bx0 + 8.0f, bcy = (float)by0 + 2.0f;
+    // weight scale 2^(14 - e) when the frame's largest weight has exponent e >= 14
+    const int we = (int)((args.status->wmax_frame_bits >> 23) & 0xFFu) - 127;
+    const float wscale = we >= 14 ? __int_as_float((127 + 14 - we) << 23) : 1.0f;
+
+    f2 pxc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pxc[i] = pk((float)(xb + 2 * i) + 0.5f, (float)(xb + 2 * i) + 1.5f);
+    const f2 pyc = pk((float)py + 0.5f, (float)py + 0.5f);
+    const float kq = -0.72134752044448170f;  // -log2(e) / 2
+    const f2 kq2 = pk(kq, kq);
+    f2 T[4];
+    float D[4][4];
+    int cnt[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        T[i] = pk(1.0f, 1.0f);
+        D[i][0] = D[i][1] = D[i][2] = D[i][3] = 0.0f;
+        cnt[2 * i] = cnt[2 * i + 1] = 0;
+    }
+
+    int head = 0, count = 0;   // unprocessed candidates: ring slots [head, head + count)
+    float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f), b_n = a_n, c_n = a_n;
+    if (start + lane < end) {
+        const uint32_t gid = __ldg(&args.gids[start + lane]);
+        a_n = __ldg(&args.rec[gid].a);
+        b_n = __ldg(&args.rec[gid].b);
+        c_n = __ldg(&args.rec[gid].c);
+    }
+    for (uint32_t base = start; base < end; base += 32) {
+        const uint32_t j = base + lane;
+        const float4 a = a_n, b = b_n, c = c_n;
+        const bool cand =
+            j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bcx, bcy, 7.5f, 1.5f));
+        if (j + 32 < end) {
+            const uint32_t gid = __ldg(&args.gids[j + 32]);
+            a_n = __ldg(&args.rec[gid].a);
+            b_n = __ldg(&args.rec[gid].b);
+            c_n = __ldg(&args.rec[gid].c);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (cand) {
+            const int pos = (head + count + __popc(bal & ((1u << lane) - 1u))) % kRing;
+            sm.geo[warp][0][pos] = make_ulonglong2(pk(a.x, a.x), pk(a.y, a.y));
+            sm.geo[warp][1][pos] = make_ulonglong2(pk(a.z, a.z), pk(a.w, a.w));
+            sm.geo[warp][2][pos] = make_ulonglong2(pk(b.x, b.x), pk(b.y, b.y));
+            const float w4[4] = {b.w * wscale, c.x * wscale, c.y * wscale, b.z * wscale};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const __half hi = __float2half_rn(w4[k]);
+                wt[k][pos] = hi;
+                wt[k + 4][pos] = __float2half_rn(w4[k] - __half2float(hi));
+            }
+        }
+        __syncwarp();
+        count += __popc(bal);
+        while (count >= 16) {
+            tc_chunk<kCount>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+            head = head + 16 == kRing ? 0 : head + 16;
+            count -= 16;
+        }
+        __syncwarp();
+    }
+    if (count > 0) {
+        // pad the last chunk with entries that include no pixel and weigh 0
+        if (lane < 16 - count) {
+            const int pos = (head + count + lane) % kRing;
+            const float far = 1e30f;
+            sm.geo[warp][0][pos] = make_ulonglong2(pk(far, far), pk(far, far));
+            sm.geo[warp][1][pos] = make_ulonglong2(pk(1.0f, 1.0f), 0ull);
+            sm.geo[warp][2][pos] = make_ulonglong2(pk(1.0f, 1.0f), 0ull);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) wt[k][pos] = __float2half_rn(0.0f);
+        }
+        __syncwarp();
+        tc_chunk<kCount>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+    }
+
+    // Quad reduction: columns c and c + 4 (lanes t, t ^ 2), then swap halves
+    // (lanes t, t ^ 1); T and counts multiply / add over the four lanes.
+    float v[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[i][k] = D[i][k] + __shfl_xor_sync(0xffffffffu, D[i][k], 2);
+    float o[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[i][k] = __shfl_xor_sync(0xffffffffu, v[i][k], 1);
+    float tt[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        upk(T[i], tt[2 * i], tt[2 * i + 1]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        tt[k] *= __shfl_xor_sync(0xffffffffu, tt[k], 1);
+        tt[k] *= __shfl_xor_sync(0xffffffffu, tt[k], 2);
+        if (kCount) {
+            cnt[k] += __shfl_xor_sync(0xffffffffu, cnt[k], 1);
+            cnt[k] += __shfl_xor_sync(0xffffffffu, cnt[k], 2);
+        }
+    }
+    if (py >= cam.height) return;
+    const float inv = 1.0f / wscale;
+    const int64_t HW = (int64_t)cam.width * cam.height;
+    const bool even = (t & 1) == 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i != t) continue;   // lane t writes pixels 2t, 2t + 1
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int x = xb + 2 * i + h;
+            if (x >= cam.width) break;
+            // v / o: (A_r, A_g) on even lanes, (A_b, B) on odd lanes; k = 2h, 2h + 1
+            const float ar = (even ? v[i][2 * h] : o[i][2 * h]) * inv;
+            const float ag = (even ? v[i][2 * h + 1] : o[i][2 * h + 1]) * inv;
+            const float ab = (even ? o[i][2 * h] : v[i][2 * h]) * inv;
+            const float bb = (even ? o[i][2 * h + 1] : v[i][2 * h + 1]) * inv;
+            const float tr = tt[2 * i + h];
+            const int64_t p = (int64_t)py * cam.width + x;
+            const float fg = bb > 0.0f ? (1.0f - tr) / bb : 0.0f;
+            float *out = args.out_rgb + 3 * p;
+            out[0] = fmaf(fg, ar, tr * args.bg[0]);
+            out[1] = fmaf(fg, ag, tr * args.bg[1]);
+            out[2] = fmaf(fg, ab, tr * args.bg[2]);
+            if (kAux) {
+                args.out_aux[p] = ar;
+                args.out_aux[HW + p] = ag;
+                args.out_aux[2 * HW + p] = ab;
+                args.out_aux[3 * HW + p] = bb;
+                args.out_aux[4 * HW + p] = tr;
+            }
+            if (kCount) args.out_count[p] = cnt[2 * i + h];
+        }
+    }
+}
+
+// Tensor-core accumulation is used for FP16-attribute scenes unless the
+// caller asks for the FP32 FMA sums.
+__host__ __device__ __forceinline__ bool use_tc(const RenderArgs &a) {
+    return a.precision == MGS_PREC_FP16 && (a.flags & MGS_FLAG_RASTER_FMA) == 0;
+}
+
 template <bool kAux, bool kCount>
 __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
     __shared__ ulonglong2 buf[kWarps][5][32];
@@ -204,15 +466,27 @@ __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
     raster_tile<kAux, kCount>(args, (int)args.tile_order[blockIdx.x], buf);
 }
 
+template <bool kAux, bool kCount>
+__global__ void __launch_bounds__(kTcThreads) k_raster_tc(RenderArgs args) {
+    __shared__ TcSmem sm;
+    if (args.status->last_pairs > args.capacity) return;  // overflowed: lists incomplete
+    raster_tile_tc<kAux, kCount>(args, (int)args.tile_order[blockIdx.x], sm);
+}
+
 // Persistent, batched: the tiles of several views (different scenes and
 // resolutions) form one work list; resident CTAs pull (view, tile) items from
 // an atomic counter until the list is exhausted.  Items are numbered view by
 // view (prefix[v] = first item of view v), each view's tiles longest first.
-__global__ void __launch_bounds__(kThreads) k_raster_batch(const RenderArgs *__restrict__ views,
-                                                           const int *__restrict__ prefix,
-                                                           int nviews,
-                                                           unsigned *__restrict__ counter) {
-    __shared__ ulonglong2 buf[kWarps][5][32];
+// A CTA has four warps: FP16 views use all four (tensor-core sums), FP32
+// views the first two (FMA sums).
+__global__ void __launch_bounds__(kTcThreads) k_raster_batch(const RenderArgs *__restrict__ views,
+                                                             const int *__restrict__ prefix,
+                                                             int nviews,
+                                                             unsigned *__restrict__ counter) {
+    __shared__ union {
+        ulonglong2 buf[kWarps][5][32];
+        TcSmem tc;
+    } sm;
     __shared__ int item_s;
     const int total = prefix[nviews];
     for (;;) {
@@ -228,14 +502,21 @@ __global__ void __launch_bounds__(kThreads) k_raster_batch(const RenderArgs *__r
         }
         const RenderArgs &a = views[lo];
         if (a.status->last_pairs > a.capacity) continue;   // that view overflowed
-        raster_tile<false, false>(a, (int)a.tile_order[item - prefix[lo]], buf);
+        const int tile = (int)a.tile_order[item - prefix[lo]];
+        if (use_tc(a))
+            raster_tile_tc<false, false>(a, tile, sm.tc);
+        else if (threadIdx.x < kThreads)
+            raster_tile<false, false>(a, tile, sm.buf);
     }
 }
 
 template <bool kAux, bool kCount>
 cudaError_t launch_t(const RenderArgs &a, cudaStream_t stream) {
     const int T = a.cam.tiles_x * a.cam.tiles_y;
-    k_raster<kAux, kCount><<<T, kThreads, 0, stream>>>(a);
+    if (use_tc(a))
+        k_raster_tc<kAux, kCount><<<T, kTcThreads, 0, stream>>>(a);
+    else
+        k_raster<kAux, kCount><<<T, kThreads, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -258,11 +539,11 @@ cudaError_t launch_raster_batch(const RenderArgs *views_dev, const int *prefix_d
     cudaError_t e = cudaMemsetAsync(counter_dev, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_batch, kThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_batch, kTcThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    k_raster_batch<<<sm_count * per_sm, kThreads, 0, stream>>>(views_dev, prefix_dev, nviews,
-                                                               counter_dev);
+    k_raster_batch<<<sm_count * per_sm, kTcThreads, 0, stream>>>(views_dev, prefix_dev, nviews,
+                                                                 counter_dev);
     return cudaGetLastError();
 }
 
