@@ -86,6 +86,9 @@ def lib():
             L.orc_rasterize.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int,
                                         ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                         P, P, P]
+            L.orc_rasterize_depth.restype = ctypes.c_int
+            L.orc_rasterize_depth.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
             L.orc_rasterize_sorted.restype = ctypes.c_int
             L.orc_rasterize_sorted.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int,
                                                ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P]
@@ -187,6 +190,27 @@ def render(attrs, cam, mlp=None, use_mlp=False, rgb_residual=False, bg=(0.0, 0.0
     rgb, aux, cnt = rasterize(g, offsets, gids, cam.width, cam.height, bg, tile_range,
                               want_aux, want_count)
     return dict(gauss=g, offsets=offsets, gids=gids, rgb=rgb, aux=aux, count=cnt)
+
+
+def rasterize_depth(g: np.ndarray, offsets, gids, width: int, height: int, tile_range=None):
+    """Depth image for Eq. 5: D = sum d a w / sum a w per pixel (0 if empty)."""
+    tx, ty = tiles(width, height)
+    t0, t1 = (0, tx * ty) if tile_range is None else tile_range
+    depth = np.zeros((height, width), np.float64)
+    gids = np.ascontiguousarray(gids, np.int32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    lib().orc_rasterize_depth(len(g), _ptr(g), _ptr(offsets),
+                              _ptr(gids if len(gids) else np.zeros(1, np.int32)),
+                              width, height, t0, t1, _ptr(depth))
+    return depth
+
+
+def render_depth(attrs, cam, mlp=None, use_mlp=False, rgb_residual=False, tile_range=None):
+    """preprocess -> bin -> depth image (Sec. 3.2, Eq. 5)."""
+    g = preprocess(attrs, cam, mlp, use_mlp, rgb_residual)
+    offsets, gids = bin_tiles(g, cam.width, cam.height)
+    return dict(gauss=g, offsets=offsets, gids=gids,
+                depth=rasterize_depth(g, offsets, gids, cam.width, cam.height, tile_range))
 
 
 def rotation(q) -> np.ndarray:

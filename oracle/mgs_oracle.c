@@ -439,6 +439,39 @@ int orc_rasterize(int64_t n, const orc_gauss *g, const int64_t *offsets,
     return 0;
 }
 
+/* Sec. 3.2, Eq. 5 reading: the depth image the distillation loss compares is
+ * the depth-aware weighted mean depth, D = sum_i d_i a_i w_i / sum_i a_i w_i,
+ * over the Gaussians included at the pixel (Eq. 2's weights a_i w_i). */
+int orc_rasterize_depth(int64_t n, const orc_gauss *g, const int64_t *offsets,
+                        const int32_t *gids, int width, int height,
+                        int tile_begin, int tile_end, double *out_depth)
+{
+    (void)n;
+    const int tiles_x = (width + ORC_TILE - 1) / ORC_TILE;
+    for (int t = tile_begin; t < tile_end; ++t) {
+        const int tx = t % tiles_x, ty = t / tiles_x;
+        for (int py = ty * ORC_TILE; py < (ty + 1) * ORC_TILE && py < height; ++py)
+            for (int px = tx * ORC_TILE; px < (tx + 1) * ORC_TILE && px < width; ++px) {
+                double Ad = 0.0, B = 0.0;
+                for (int64_t k = offsets[t]; k < offsets[t + 1]; ++k) {
+                    const orc_gauss *gi = g + gids[k];
+                    if (!orc_includes(gi, px, py)) continue;
+                    double dx = px + 0.5 - gi->mean[0];
+                    double dy = py + 0.5 - gi->mean[1];
+                    double q = gi->conic[0] * dx * dx + 2.0 * gi->conic[1] * dx * dy +
+                               gi->conic[2] * dy * dy;
+                    double alpha = gi->opacity * exp(-0.5 * q);
+                    if (alpha > 0.99) alpha = 0.99;
+                    double aw = alpha * gi->weight;
+                    Ad += gi->depth * aw;
+                    B += aw;
+                }
+                out_depth[(int64_t)py * width + px] = B > 0.0 ? Ad / B : 0.0;
+            }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Included pairs (for the differentiable FP64 restatement in grad.py)         */
 /* ------------------------------------------------------------------------- */

@@ -107,6 +107,14 @@ int orc_includes(const orc_gauss *g, int px, int py);
  * out_rgb: H x W x 3.  out_aux (optional): 5 x H x W planes
  * (A_r, A_g, A_b, B, T) with A = sum c a w, B = sum a w, T = prod (1 - a).
  * out_count (optional): H x W number of included Gaussians. */
+/* Rendered depth for the depth distillation of Sec. 3.2 (Eq. 5): the
+ * depth-aware weighted mean of the included Gaussians' view depths,
+ * D = sum d a w / sum a w (0 where nothing is included), with the same
+ * inclusion test, alpha and weights as Eq. 2.  out_depth: H x W. */
+int orc_rasterize_depth(int64_t n, const orc_gauss *g, const int64_t *offsets,
+                        const int32_t *gids, int width, int height,
+                        int tile_begin, int tile_end, double *out_depth);
+
 int orc_rasterize(int64_t n, const orc_gauss *g, const int64_t *offsets,
                   const int32_t *gids, int width, int height,
                   const double bg[3], int tile_begin, int tile_end,
