@@ -51,7 +51,10 @@ class _Camera(ctypes.Structure):
 class _MLP(ctypes.Structure):
     _fields_ = [("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p),
                 ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p),
-                ("w3", ctypes.c_void_p), ("b3", ctypes.c_void_p)]
+                ("w3", ctypes.c_void_p), ("b3", ctypes.c_void_p),
+                ("w4", ctypes.c_void_p), ("b4", ctypes.c_void_p),
+                ("h1", ctypes.c_int32), ("h2", ctypes.c_int32), ("h3", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 GAUSS_DTYPE = np.dtype([
@@ -122,15 +125,28 @@ class _MLPHolder:
     """Keeps the contiguous weight arrays alive while the C struct points at them."""
 
     def __init__(self, mlp):
+        w4 = getattr(mlp, "w4", None)
         self.arrays = [np.ascontiguousarray(mlp.w1, np.uint16),
                        np.ascontiguousarray(mlp.b1, np.float32),
                        np.ascontiguousarray(mlp.w2, np.uint16),
                        np.ascontiguousarray(mlp.b2, np.float32),
                        np.ascontiguousarray(mlp.w3, np.uint16),
                        np.ascontiguousarray(mlp.b3, np.float32)]
-        assert self.arrays[0].shape == (64, 22) and self.arrays[2].shape == (64, 64)
-        assert self.arrays[4].shape == (5, 64)
-        self.s = _MLP(*[a.ctypes.data for a in self.arrays])
+        if w4 is None:
+            assert self.arrays[0].shape == (64, 22) and self.arrays[2].shape == (64, 64)
+            assert self.arrays[4].shape == (5, 64)
+            dims = (0, 0, 0)
+            self.arrays += [None, None]
+        else:
+            h1, h2, h3 = self.arrays[0].shape[0], self.arrays[2].shape[0], self.arrays[4].shape[0]
+            assert self.arrays[0].shape == (h1, 22) and self.arrays[2].shape == (h2, h1)
+            assert self.arrays[4].shape == (h3, h2) and np.shape(w4) == (5, h3)
+            assert max(h1, h2, h3) <= 256
+            dims = (h1, h2, h3)
+            self.arrays += [np.ascontiguousarray(w4, np.uint16),
+                            np.ascontiguousarray(mlp.b4, np.float32)]
+        ptrs = [a.ctypes.data if a is not None else None for a in self.arrays]
+        self.s = _MLP(*ptrs, *dims, 0)
 
 
 def tiles(width: int, height: int) -> tuple[int, int]:

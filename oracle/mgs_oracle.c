@@ -74,30 +74,45 @@ static double bf16_bits_to_double(uint16_t b)
 /* Eq. 4.  MLP_f = two ReLU layers (22 -> 64 -> 64); MLP_phi and MLP_o (and the
  * optional colour residual) are the rows of one linear head (64 -> 5).  The
  * tensor-core inputs (x, h1, h2) are rounded to BF16; everything else FP64. */
+/* One hidden layer: out = BF16(ReLU(W in + b)), in and W as given. */
+static void hidden_layer(const uint16_t *w, const float *b, const double *in, int n_in,
+                         int n_out, double *out)
+{
+    for (int j = 0; j < n_out; ++j) {
+        double acc = 0.0;
+        for (int i = 0; i < n_in; ++i)
+            acc += bf16_bits_to_double(w[j * n_in + i]) * in[i];
+        acc += (double)b[j];
+        out[j] = orc_bf16_round(acc > 0.0 ? acc : 0.0);
+    }
+}
+
 void orc_mlp_eval(const orc_mlp *mlp, const double x[22], double out[5])
 {
-    double xr[22], h1[64], h2[64];
+    /* Eq. 4 with BF16 inputs to every layer: F = MLP_f([P, s, q, Y]), then the
+     * phi and o heads (and the optional colour residual rows). */
+    double xr[22], ha[256], hb[256];
     for (int i = 0; i < 22; ++i) xr[i] = orc_bf16_round(x[i]);
-    for (int j = 0; j < 64; ++j) {
-        double acc = 0.0;
-        for (int i = 0; i < 22; ++i)
-            acc += bf16_bits_to_double(mlp->w1[j * 22 + i]) * xr[i];
-        acc += (double)mlp->b1[j];
-        h1[j] = orc_bf16_round(acc > 0.0 ? acc : 0.0);
-    }
-    for (int j = 0; j < 64; ++j) {
-        double acc = 0.0;
-        for (int i = 0; i < 64; ++i)
-            acc += bf16_bits_to_double(mlp->w2[j * 64 + i]) * h1[i];
-        acc += (double)mlp->b2[j];
-        h2[j] = orc_bf16_round(acc > 0.0 ? acc : 0.0);
+    const uint16_t *wh;
+    const float *bh;
+    int nh;
+    const double *last;
+    if (mlp->h1 == 0) {
+        hidden_layer(mlp->w1, mlp->b1, xr, 22, 64, ha);
+        hidden_layer(mlp->w2, mlp->b2, ha, 64, 64, hb);
+        wh = mlp->w3; bh = mlp->b3; nh = 64; last = hb;
+    } else {
+        hidden_layer(mlp->w1, mlp->b1, xr, 22, mlp->h1, ha);
+        hidden_layer(mlp->w2, mlp->b2, ha, mlp->h1, mlp->h2, hb);
+        hidden_layer(mlp->w3, mlp->b3, hb, mlp->h2, mlp->h3, ha);
+        wh = mlp->w4; bh = mlp->b4; nh = mlp->h3; last = ha;
     }
     double y[5];
     for (int k = 0; k < 5; ++k) {
         double acc = 0.0;
-        for (int i = 0; i < 64; ++i)
-            acc += bf16_bits_to_double(mlp->w3[k * 64 + i]) * h2[i];
-        y[k] = acc + (double)mlp->b3[k];
+        for (int i = 0; i < nh; ++i)
+            acc += bf16_bits_to_double(wh[k * nh + i]) * last[i];
+        y[k] = acc + (double)bh[k];
     }
     out[0] = y[0] > 0.0 ? y[0] : 0.0;          /* phi = ReLU(MLP_phi F) */
     out[1] = 1.0 / (1.0 + exp(-y[1]));         /* o = sigmoid(MLP_o F)  */

@@ -46,12 +46,18 @@ typedef struct {
     float znear;
 } orc_camera;
 
-/* Enhancement MLP (Eq. 4): 22 -> 64 -> 64 -> 5 (phi, o, d_r, d_g, d_b).
- * Weights are BF16 bit patterns, row-major [out][in]; biases FP32. */
+/* Enhancement MLP (Eq. 4), head rows (phi, o, d_r, d_g, d_b).  Weights are
+ * BF16 bit patterns, row-major [out][in]; biases FP32.
+ *   h1 == 0: 22 -> 64 -> 64 -> 5, w3/b3 the head (w4/b4 unused);
+ *   h1 != 0: 22 -> h1 -> h2 -> h3 -> 5, w4/b4 the head (App. C's MLP_f has
+ *            h = 256, 128, 64). */
 typedef struct {
-    const uint16_t *w1; const float *b1;   /* [64][22], [64] */
-    const uint16_t *w2; const float *b2;   /* [64][64], [64] */
-    const uint16_t *w3; const float *b3;   /* [5][64],  [5]  */
+    const uint16_t *w1; const float *b1;   /* [h1][22], [h1] */
+    const uint16_t *w2; const float *b2;   /* [h2][h1], [h2] */
+    const uint16_t *w3; const float *b3;   /* [h3][h2] (or the [5][64] head) */
+    const uint16_t *w4; const float *b4;   /* [5][h3], [5] */
+    int32_t h1, h2, h3;
+    int32_t pad;
 } orc_mlp;
 
 /* Per-Gaussian result of the preprocessing stage. */

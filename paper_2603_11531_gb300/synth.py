@@ -72,6 +72,16 @@ class MLPWeights:
     b2: np.ndarray   # (64,) float32
     w3: np.ndarray   # (5, 64) uint16, rows: phi, o, d_r, d_g, d_b
     b3: np.ndarray   # (5,) float32
+    # three hidden layers (App. C widths): w3 is then the third hidden layer
+    # (h3, h2) and w4 (5, h3) the head
+    w4: np.ndarray | None = None
+    b4: np.ndarray | None = None
+
+    @property
+    def hidden(self) -> tuple:
+        if self.w4 is None:
+            return (self.w1.shape[0], self.w2.shape[0])
+        return (self.w1.shape[0], self.w2.shape[0], self.w3.shape[0])
 
 
 @dataclasses.dataclass
@@ -154,11 +164,12 @@ def unbounded_scene(n: int, seed: int, precision: str = "fp16",
     return Scene(_store(a, precision))
 
 
-def random_mlp(seed: int) -> MLPWeights:
+def random_mlp(seed: int, hidden=(MLP_HIDDEN, MLP_HIDDEN)) -> MLPWeights:
     """Kaiming-uniform weights (bound sqrt(6/fan_in)) rounded to BF16; hidden
     biases U(-1/sqrt(fan_in), 1/sqrt(fan_in)); head biases (phi, o, rgb) =
     (1, 0, 0, 0, 0) so that phi starts near 1 (Sec. 3.4 initialises MLP_phi
-    to output 1)."""
+    to output 1).  `hidden` = (64, 64) or three widths such as App. C's
+    (256, 128, 64)."""
     rng = np.random.Generator(np.random.PCG64(seed))
 
     def lin(out_f, in_f):
@@ -168,11 +179,26 @@ def random_mlp(seed: int) -> MLPWeights:
         b = rng.uniform(-bb, bb, size=out_f).astype(np.float32)
         return f32_to_bf16_bits(w), b
 
-    w1, b1 = lin(MLP_HIDDEN, MLP_IN)
-    w2, b2 = lin(MLP_HIDDEN, MLP_HIDDEN)
-    w3, _ = lin(MLP_OUT, MLP_HIDDEN)
-    b3 = np.array([1.0, 0.0, 0.0, 0.0, 0.0], np.float32)
-    return MLPWeights(w1, b1, w2, b2, w3, b3)
+    head_b = np.array([1.0, 0.0, 0.0, 0.0, 0.0], np.float32)
+    if len(hidden) == 2 and tuple(hidden) == (MLP_HIDDEN, MLP_HIDDEN):
+        w1, b1 = lin(MLP_HIDDEN, MLP_IN)
+        w2, b2 = lin(MLP_HIDDEN, MLP_HIDDEN)
+        w3, _ = lin(MLP_OUT, MLP_HIDDEN)
+        return MLPWeights(w1, b1, w2, b2, w3, head_b)
+    h1, h2, h3 = (int(h) for h in hidden)
+    w1, b1 = lin(h1, MLP_IN)
+    w2, b2 = lin(h2, h1)
+    w3, b3 = lin(h3, h2)
+    w4, _ = lin(MLP_OUT, h3)
+    return MLPWeights(w1, b1, w2, b2, w3, b3, w4, head_b)
+
+
+PAPER_MLP_HIDDEN = (256, 128, 64)   # App. C: MLP_f widths
+
+
+def random_mlp_paper(seed: int) -> MLPWeights:
+    """random_mlp with the paper's MLP_f widths 256, 128, 64 (App. C)."""
+    return random_mlp(seed, PAPER_MLP_HIDDEN)
 
 
 # ----------------------------------------------------------------------------

@@ -417,6 +417,56 @@ def test_mlp_matches_torch_linear(oracle_lib):
             np.testing.assert_allclose(oracle.mlp_eval(mlp, x), exp, rtol=1e-12, atol=1e-12)
 
 
+def test_paper_width_mlp_matches_torch_linear(oracle_lib):
+    """App. C's MLP_f (22 -> 256 -> 128 -> 64, then the phi / o heads):
+    the oracle's generic layers against a torch nn.Linear chain in FP64 with
+    the same BF16 rounding of every layer input."""
+    torch = pytest.importorskip("torch")
+    mlp = synth.random_mlp_paper(19)
+    assert mlp.hidden == (256, 128, 64)
+    rng = np.random.default_rng(16)
+
+    def lin(bits, b):
+        wt = torch.from_numpy(synth.bf16_bits_to_f32(bits).astype(np.float64))
+        m = torch.nn.Linear(wt.shape[1], wt.shape[0], dtype=torch.float64)
+        with torch.no_grad():
+            m.weight.copy_(wt)
+            m.bias.copy_(torch.from_numpy(np.asarray(b, np.float64)))
+        return m
+
+    def bf(t):
+        return t.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+
+    layers = [lin(mlp.w1, mlp.b1), lin(mlp.w2, mlp.b2), lin(mlp.w3, mlp.b3)]
+    head = lin(mlp.w4, mlp.b4)
+    with torch.no_grad():
+        for _ in range(32):
+            x = rng.normal(0, 0.6, 22).astype(np.float32).astype(np.float64)
+            h = bf(torch.from_numpy(x))
+            for l in layers:
+                h = bf(torch.relu(l(h)))
+            y = head(h)
+            exp = np.array([max(0.0, y[0].item()), torch.sigmoid(y[1]).item(), y[2].item(),
+                            y[3].item(), y[4].item()])
+            np.testing.assert_allclose(oracle.mlp_eval(mlp, x), exp, rtol=1e-12, atol=1e-12)
+
+
+def test_paper_width_mlp_zero_weights_reduce_to_plain(oracle_lib):
+    """Zero weights in every layer of the paper-width MLP: the render equals
+    the plain render with phi = ReLU(b_phi), o = sigmoid(b_o)."""
+    mlp = synth.random_mlp_paper(3)
+    for k in ("w1", "w2", "w3", "w4"):
+        setattr(mlp, k, np.zeros_like(getattr(mlp, k)))
+    b_o = -0.3
+    mlp.b4 = np.array([1.0, b_o, 0.0, 0.0, 0.0], np.float32)
+    attrs = _small_scene(120).astype(np.float64)
+    attrs[:, 10] = 1.0 / (1.0 + math.exp(-b_o))
+    cam = synth.look_at((0, 0.2, -3), (0, 0, 0), 40, 40, 60.0)
+    a = oracle.render(attrs, cam, mlp=mlp, use_mlp=True)
+    b = oracle.render(attrs, cam)
+    np.testing.assert_allclose(a["rgb"], b["rgb"], atol=1e-12)
+
+
 def test_mlp_zero_weights_reduce_to_plain(oracle_lib):
     """Zero weights: phi = ReLU(b_phi), o = sigmoid(b_o), so the MLP render
     equals the plain render of a scene whose stored opacities are sigmoid(b_o)."""
