@@ -191,6 +191,16 @@ mgs_status mgs_render_checked(mgs_workspace ws, mgs_scene scene,
                               float *out_aux, int32_t *out_count,
                               mgs_stream stream);
 
+/* Depth image for the depth distillation of Sec. 3.2 (Eq. 5): renders the
+ * colour image into out_rgb (as mgs_render) and the depth-aware weighted mean
+ * view depth D = sum d_i a_i w_i / sum a_i w_i (Eq. 2's weights; 0 where no
+ * Gaussian is included) into out_depth (device, height x width FP32).  The
+ * sums use FP32 FMAs for every precision.  MGS_FLAG_SORTED is not accepted.
+ * Errors: MGS_ERR_INVALID_ARG for a NULL out_depth, otherwise as mgs_render. */
+mgs_status mgs_render_depth(mgs_workspace ws, mgs_scene scene,
+                            const mgs_camera *cam, const mgs_render_opts *opts,
+                            float *out_rgb, float *out_depth, mgs_stream stream);
+
 /* End-to-end render into HOST memory: renders into a workspace-owned device
  * image and copies it to host_rgb (height x width x 3 FP32; pinned memory
  * gives an asynchronous copy).  Asynchronous on `stream` like mgs_render. */

@@ -41,7 +41,7 @@ EXPORTS = (
     "mgs_workspace_reserve", "mgs_workspace_bytes", "mgs_workspace_sync", "mgs_render",
     "mgs_render_checked", "mgs_render_to_host", "mgs_tile_lists", "mgs_last_error",
     "mgs_version", "mgs_workspace_set_timing", "mgs_workspace_stage_times",
-    "mgs_render_static", "mgs_render_backward",
+    "mgs_render_static", "mgs_render_backward", "mgs_render_depth",
     "mgs_server_create", "mgs_server_destroy", "mgs_server_submit", "mgs_server_wait",
     "mgs_server_ticket", "mgs_server_stats", "mgs_now",
 )
@@ -104,6 +104,8 @@ def lib():
                                         ctypes.POINTER(mgs_render_opts), P, P, P, P], I32),
                 "mgs_render_to_host": ([P, P, ctypes.POINTER(mgs_camera),
                                         ctypes.POINTER(mgs_render_opts), P, P], I32),
+                "mgs_render_depth": ([P, P, ctypes.POINTER(mgs_camera),
+                                      ctypes.POINTER(mgs_render_opts), P, P, P], I32),
                 "mgs_tile_lists": ([P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P], I32),
                 "mgs_workspace_set_timing": ([P, I32], I32),
                 "mgs_workspace_stage_times": ([P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], I32),
@@ -267,6 +269,12 @@ def mgs_render_checked(ws, scene, cam, opts, out_rgb, out_aux=None, out_count=No
                                     _ptr(out_aux), _ptr(out_count), _stream(stream)))
 
 
+def mgs_render_depth(ws, scene, cam, opts, out_rgb, out_depth, stream=None):
+    c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    _check(lib().mgs_render_depth(ws, scene, ctypes.byref(c), ctypes.byref(opts), _ptr(out_rgb),
+                                  _ptr(out_depth), _stream(stream)))
+
+
 def mgs_render_to_host(ws, scene, cam, opts, host_rgb, stream=None):
     c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
     _check(lib().mgs_render_to_host(ws, scene, ctypes.byref(c), ctypes.byref(opts),
@@ -358,6 +366,23 @@ class Renderer:
         fn = mgs_render_checked if checked else mgs_render
         fn(self.ws, scene, cam, opts, rgb, a, c, stream)
         return {"rgb": rgb, "aux": a, "count": c}
+
+    def render_depth(self, scene, cam, use_mlp=False, rgb_residual=False, flags=0, stream=None):
+        """Colour and depth image (Eq. 5 depth), then a workspace sync."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        H, W = int(cam.height), int(cam.width)
+        rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+        opts = render_opts(use_mlp, rgb_residual, (0.0, 0.0, 0.0), flags)
+        for attempt in range(2):
+            mgs_render_depth(self.ws, scene, cam, opts, rgb, depth, stream)
+            st, _ = mgs_workspace_sync(self.ws, stream, allow_overflow=True)
+            if st == MGS_OK:
+                break
+        if st != MGS_OK:
+            raise MGSError(st, "depth render overflowed its tile lists twice")
+        return {"rgb": rgb, "depth": depth}
 
     def tile_lists(self, stream=None):
         """Copies of the last render's tile lists as numpy arrays (offsets, gids)."""

@@ -208,7 +208,8 @@ struct BackwardIO {
 mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
                        const mgs_render_opts *opts, float *out_rgb, float *out_aux,
                        int32_t *out_count, cudaStream_t stream,
-                       const BackwardIO *bwd = nullptr, RenderArgs *prep = nullptr) {
+                       const BackwardIO *bwd = nullptr, RenderArgs *prep = nullptr,
+                       float *out_depth = nullptr) {
     if (!w || !s) return fail(MGS_ERR_INVALID_ARG, "workspace or scene is NULL");
     if (w->ctx != s->ctx) return fail(MGS_ERR_INVALID_ARG, "scene and workspace belong to different contexts");
     mgs_status st = check_camera(cam);
@@ -252,6 +253,9 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     a.out_rgb = out_rgb;
     a.out_aux = out_aux;
     a.out_count = out_count;
+    a.out_depth = out_depth;
+    if (out_depth && (out_aux || out_count || (opts->flags & MGS_FLAG_SORTED)))
+        return fail(MGS_ERR_INVALID_ARG, "the depth image is rendered without aux, counts or sorting");
 
     std::array<cudaEvent_t, 4> ev{};
     cudaError_t e = cudaSuccess;
@@ -597,6 +601,14 @@ mgs_status mgs_render(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
                       int32_t *out_count, mgs_stream stream) {
     return render_impl(w, s, cam, opts, out_rgb, out_aux, out_count,
                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+mgs_status mgs_render_depth(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
+                            const mgs_render_opts *opts, float *out_rgb, float *out_depth,
+                            mgs_stream stream) {
+    if (!out_depth) return fail(MGS_ERR_INVALID_ARG, "out_depth is NULL");
+    return render_impl(w, s, cam, opts, out_rgb, nullptr, nullptr,
+                       reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr, out_depth);
 }
 
 mgs_status mgs_render_backward(mgs_workspace w, mgs_scene s, const mgs_camera *cam,

@@ -90,6 +90,7 @@ struct RenderArgs {
     float *out_rgb;
     float *out_aux;
     int32_t *out_count;
+    float *out_depth;          // depth image (Eq. 5), optional
 };
 
 // Can Gaussian (m, l) include any pixel centre of the block centred at (bx, by)

@@ -62,10 +62,10 @@ __device__ __forceinline__ float ex2(float x) {
 //   s4 = {-w c_g, -w c_g, -w c_b, -w c_b}
 
 // Accumulates one staged Gaussian into a thread's four pixels (two pairs).
-template <bool kCount>
+template <bool kCount, bool kDepth>
 __device__ __forceinline__ void accumulate(const ulonglong2 (*wb)[32], int k, f2 pxa, f2 pxb,
                                            f2 pyc, f2 kq2, f2 (&A)[2][3], f2 (&B)[2],
-                                           f2 (&T)[2], int (&cnt)[4]) {
+                                           f2 (&T)[2], f2 (&AD)[2], int (&cnt)[4]) {
     const ulonglong2 s0 = wb[0][k], s1 = wb[1][k], s2 = wb[2][k];
     // inclusion test (exact FP32 sequence); the row terms are shared by both pairs
     const f2 dy = sub2(pyc, s0.y);
@@ -101,6 +101,11 @@ __device__ __forceinline__ void accumulate(const ulonglong2 (*wb)[32], int k, f2
         B[h] = fma2(na[h], s3.x, B[h]);
         T[h] = fma2(na[h], T[h], T[h]);
     }
+    if (kDepth) {
+        const ulonglong2 s5 = wb[5][k];   // {-w d, -w d, 0, 0}
+        AD[0] = fma2(na[0], s5.x, AD[0]);
+        AD[1] = fma2(na[1], s5.x, AD[1]);
+    }
 }
 
 // Rasterises one tile with one CTA (two warps); warp w owns the 16x8 pixel
@@ -110,9 +115,9 @@ __device__ __forceinline__ void accumulate(const ulonglong2 (*wb)[32], int k, f2
 // the current ones are accumulated), are tested against the warp's block,
 // compacted into the warp's shared-memory buffer (ballot) and accumulated by
 // all lanes.
-template <bool kAux, bool kCount>
+template <bool kAux, bool kCount, bool kDepth = false>
 __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
-                                            ulonglong2 (*buf)[5][32]) {
+                                            ulonglong2 (*buf)[kDepth ? 6 : 5][32]) {
     const DevCamera &cam = args.cam;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -133,6 +138,7 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
     f2 A[2][3] = {{0ull, 0ull, 0ull}, {0ull, 0ull, 0ull}};
     f2 B[2] = {0ull, 0ull};
     f2 T[2] = {pk(1.0f, 1.0f), pk(1.0f, 1.0f)};
+    f2 AD[2] = {0ull, 0ull};
     int cnt[4] = {0, 0, 0, 0};
     ulonglong2(*wb)[32] = buf[warp];
 
@@ -162,19 +168,24 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
             wb[2][pos] = make_ulonglong2(pk(b.x, b.x), pk(b.y, b.y));
             wb[3][pos] = make_ulonglong2(pk(b.z, b.z), pk(b.w, b.w));
             wb[4][pos] = make_ulonglong2(pk(c.x, c.x), pk(c.y, c.y));
+            if (kDepth) {
+                const float wd = b.z * c.z;   // -w d
+                wb[5][pos] = make_ulonglong2(pk(wd, wd), 0ull);
+            }
         }
         __syncwarp();
         const int nc = __popc(bal);
 #pragma unroll 2
         for (int k = 0; k < nc; ++k)
-            accumulate<kCount>(wb, k, pxa, pxb, pyc, kq2, A, B, T, cnt);
+            accumulate<kCount, kDepth>(wb, k, pxa, pxb, pyc, kq2, A, B, T, AD, cnt);
         __syncwarp();
     }
 
     if (py >= cam.height) return;
-    float ar[4], ag[4], ab[4], bb[4], tt[4];
+    float ar[4], ag[4], ab[4], bb[4], tt[4], ad[4];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+        upk(AD[h], ad[2 * h], ad[2 * h + 1]);
         upk(A[h][0], ar[2 * h], ar[2 * h + 1]);
         upk(A[h][1], ag[2 * h], ag[2 * h + 1]);
         upk(A[h][2], ab[2 * h], ab[2 * h + 1]);
@@ -200,6 +211,7 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
             args.out_aux[4 * HW + p] = tt[k];
         }
         if (kCount) args.out_count[p] = cnt[k];
+        if (kDepth) args.out_depth[p] = bb[k] > 0.0f ? ad[k] / bb[k] : 0.0f;
     }
 }
 
@@ -459,11 +471,11 @@ __host__ __device__ __forceinline__ bool use_tc(const RenderArgs &a) {
     return a.precision == MGS_PREC_FP16 && (a.flags & MGS_FLAG_RASTER_FMA) == 0;
 }
 
-template <bool kAux, bool kCount>
+template <bool kAux, bool kCount, bool kDepth = false>
 __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
-    __shared__ ulonglong2 buf[kWarps][5][32];
+    __shared__ ulonglong2 buf[kWarps][kDepth ? 6 : 5][32];
     if (args.status->last_pairs > args.capacity) return;  // overflowed: lists incomplete
-    raster_tile<kAux, kCount>(args, (int)args.tile_order[blockIdx.x], buf);
+    raster_tile<kAux, kCount, kDepth>(args, (int)args.tile_order[blockIdx.x], buf);
 }
 
 template <bool kAux, bool kCount>
@@ -524,6 +536,10 @@ cudaError_t launch_t(const RenderArgs &a, cudaStream_t stream) {
 
 cudaError_t launch_raster(const RenderArgs &a, cudaStream_t stream) {
     const bool aux = a.out_aux != nullptr, cnt = a.out_count != nullptr;
+    if (a.out_depth) {   // depth image (Eq. 5): FMA sums, no aux / count outputs
+        k_raster<false, false, true><<<a.cam.tiles_x * a.cam.tiles_y, kThreads, 0, stream>>>(a);
+        return cudaGetLastError();
+    }
     if (aux && cnt) return launch_t<true, true>(a, stream);
     if (aux) return launch_t<true, false>(a, stream);
     if (cnt) return launch_t<false, true>(a, stream);
