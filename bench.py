@@ -322,6 +322,8 @@ def run_gpu(args):
             line["serving"] = run_serving(m, torch, local)
         if world == 1 and not args.no_large:
             line["large"] = run_large(m, torch, local)
+        if world == 1 and not args.no_paper_mlp:
+            line["paper_width_mlp"] = run_paper_mlp(m, torch, local)
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline_sample()
             cb.pop("seconds", None)
@@ -463,6 +465,40 @@ def run_large(m, torch, local, frames=3):
     return res
 
 
+def run_paper_mlp(m, torch, local, reps=2):
+    """The 600k workload with the paper-width MLP_f (App. C: 22 -> 256 ->
+    128 -> 64 -> heads) on tcgen05: per-frame stage times over the 64 poses
+    and the tensor throughput of the fused preprocessing + MLP kernel."""
+    from paper_2603_11531_gb300 import synth
+    scene, cams = synth.workload_unbounded_600k(n_poses=N_POSES)
+    scene.mlp = synth.random_mlp_paper(21)
+    r = m.Renderer(local)
+    h = r.load_scene(scene)
+    opts = m.render_opts(use_mlp=True)
+    out = torch.empty((cams[0].height, cams[0].width, 3), device="cuda")
+    stream = torch.cuda.Stream(device=local)
+    cs = [m.camera_struct(c) for c in cams]
+    for c in cs[:4]:
+        m.mgs_render_checked(r.ws, h, c, opts, out, None, None, stream)
+    m.mgs_workspace_stage_times(r.ws, stream)
+    m.mgs_workspace_set_timing(r.ws, True)
+    for _ in range(reps):
+        for c in cs:
+            m.mgs_render(r.ws, h, c, opts, out, None, None, stream)
+    ms, fr = m.mgs_workspace_stage_times(r.ws, stream)
+    m.mgs_workspace_set_timing(r.ws, False)
+    st, _ = m.mgs_workspace_sync(r.ws, stream, allow_overflow=True)
+    if st != m.MGS_OK:
+        raise RuntimeError("paper-width MLP run overflowed its tile lists")
+    r.close()
+    per = [x / fr for x in ms]
+    h1, h2, h3 = synth.PAPER_MLP_HIDDEN
+    flops = 2.0 * scene.n * (32 * h1 + h1 * h2 + h2 * h3)   # MMA work incl. K padding to 32
+    return {"hidden": [h1, h2, h3], "preprocess_mlp_ms": per[0], "binning_ms": per[1],
+            "raster_ms": per[2], "ms_per_frame": sum(per), "fps": 1000.0 / sum(per),
+            "mlp_tflops_in_preprocess": flops / (per[0] / 1000.0) / 1e12}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,6 +508,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-paper-mlp", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -90,7 +90,12 @@ typedef struct mgs_workspace_s *mgs_workspace;
  * Enhancement MLP (Eq. 4), optional: w1 [64][22], w2 [64][64], w3 [5][64]
  * as BF16 bit patterns, row-major [out][in]; biases b1 [64], b2 [64], b3 [5]
  * FP32.  Head rows: phi, o, d_r, d_g, d_b (the last three are an optional
- * colour residual).  MLP input: [P(3), s(3), normalised q(4), Y(12)]. */
+ * colour residual).  MLP input: [P(3), s(3), normalised q(4), Y(12)].
+ * Paper-width MLP_f (App. C: 256, 128, 64 neurons): set mlp_hidden to the
+ * three widths (each a multiple of 16 in 16..256); then w1 [h1][22],
+ * w2 [h2][h1], w3 [h3][h2] are the hidden layers, w4 [5][h3] the head, and
+ * b1..b4 their biases.  It runs on tcgen05 only and has no backward pass.
+ * mlp_hidden all zero: the 22 -> 64 -> 64 -> 5 MLP (w4, b4 unused). */
 typedef struct {
     int64_t n;              /* number of Gaussians, >= 0 */
     int32_t precision;      /* MGS_PREC_FP32 or MGS_PREC_FP16 */
@@ -102,6 +107,10 @@ typedef struct {
     const float *mlp_b2;
     const uint16_t *mlp_w3;
     const float *mlp_b3;
+    const uint16_t *mlp_w4; /* head of the paper-width MLP, else NULL */
+    const float *mlp_b4;
+    int32_t mlp_hidden[3];  /* {0, 0, 0} or three hidden widths */
+    int32_t reserved;       /* 0 */
 } mgs_scene_desc;
 
 /* Pinhole camera, world->camera (R row-major, t), OpenCV axes (x right,

@@ -72,7 +72,9 @@ class mgs_scene_desc(ctypes.Structure):
                 ("attrs_on_device", ctypes.c_int32), ("attrs", ctypes.c_void_p),
                 ("mlp_w1", ctypes.c_void_p), ("mlp_b1", ctypes.c_void_p),
                 ("mlp_w2", ctypes.c_void_p), ("mlp_b2", ctypes.c_void_p),
-                ("mlp_w3", ctypes.c_void_p), ("mlp_b3", ctypes.c_void_p)]
+                ("mlp_w3", ctypes.c_void_p), ("mlp_b3", ctypes.c_void_p),
+                ("mlp_w4", ctypes.c_void_p), ("mlp_b4", ctypes.c_void_p),
+                ("mlp_hidden", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32)]
 
 
 def lib():
@@ -216,9 +218,16 @@ def mgs_load_scene(ctx, attrs, mlp=None, stream=None):
         arrs = [np.ascontiguousarray(mlp.w1, np.uint16), np.ascontiguousarray(mlp.b1, np.float32),
                 np.ascontiguousarray(mlp.w2, np.uint16), np.ascontiguousarray(mlp.b2, np.float32),
                 np.ascontiguousarray(mlp.w3, np.uint16), np.ascontiguousarray(mlp.b3, np.float32)]
-        assert arrs[0].shape == (64, 22) and arrs[2].shape == (64, 64) and arrs[4].shape == (5, 64)
+        w4 = getattr(mlp, "w4", None)
+        if w4 is None:
+            assert arrs[0].shape == (64, 22) and arrs[2].shape == (64, 64) and arrs[4].shape == (5, 64)
+        else:
+            arrs += [np.ascontiguousarray(w4, np.uint16), np.ascontiguousarray(mlp.b4, np.float32)]
+            h1, h2, h3 = arrs[0].shape[0], arrs[2].shape[0], arrs[4].shape[0]
+            d.mlp_hidden[0], d.mlp_hidden[1], d.mlp_hidden[2] = h1, h2, h3
+            d.mlp_w4, d.mlp_b4 = arrs[6].ctypes.data, arrs[7].ctypes.data
         keep += arrs
-        (d.mlp_w1, d.mlp_b1, d.mlp_w2, d.mlp_b2, d.mlp_w3, d.mlp_b3) = [x.ctypes.data for x in arrs]
+        (d.mlp_w1, d.mlp_b1, d.mlp_w2, d.mlp_b2, d.mlp_w3, d.mlp_b3) = [x.ctypes.data for x in arrs[:6]]
     h = ctypes.c_void_p()
     _check(lib().mgs_load_scene(ctx, ctypes.byref(d), _stream(stream), ctypes.byref(h)))
     return h

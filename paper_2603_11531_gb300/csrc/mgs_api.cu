@@ -218,6 +218,11 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     if (!out_rgb && !bwd && !prep) return fail(MGS_ERR_INVALID_ARG, "out_rgb is NULL");
     if (opts->use_mlp && !s->has_mlp)
         return fail(MGS_ERR_INVALID_ARG, "use_mlp requested but the scene has no MLP weights");
+    if (opts->use_mlp && s->mlp.h1 != 0) {
+        if (opts->flags & MGS_FLAG_MLP_MMA_SYNC)
+            return fail(MGS_ERR_INVALID_ARG, "the paper-width MLP runs on tcgen05 only");
+        if (bwd) return fail(MGS_ERR_INVALID_ARG, "no backward pass for the paper-width MLP");
+    }
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(opts->bg[k])) return fail(MGS_ERR_INVALID_ARG, "bg must be finite");
     DeviceGuard g(w->ctx->device);
@@ -418,6 +423,17 @@ mgs_status mgs_load_scene(mgs_ctx ctx, const mgs_scene_desc *d, mgs_stream strea
     const bool any_mlp = d->mlp_w1 || d->mlp_b1 || d->mlp_w2 || d->mlp_b2 || d->mlp_w3 || d->mlp_b3;
     const bool all_mlp = d->mlp_w1 && d->mlp_b1 && d->mlp_w2 && d->mlp_b2 && d->mlp_w3 && d->mlp_b3;
     if (any_mlp && !all_mlp) return fail(MGS_ERR_INVALID_ARG, "MLP weights are partially given");
+    const int h1 = d->mlp_hidden[0], h2 = d->mlp_hidden[1], h3 = d->mlp_hidden[2];
+    const bool wide = h1 != 0 || h2 != 0 || h3 != 0;
+    if (wide) {
+        for (int h : {h1, h2, h3})
+            if (h < 16 || h > 256 || h % 16 != 0)
+                return fail(MGS_ERR_INVALID_ARG, "MLP widths must be multiples of 16 in 16..256");
+        if (!all_mlp || !d->mlp_w4 || !d->mlp_b4)
+            return fail(MGS_ERR_INVALID_ARG, "the paper-width MLP needs w1..w4 and b1..b4");
+        if (wide_mlp_smem(h1, h2, h3) > 227 * 1024)
+            return fail(MGS_ERR_INVALID_ARG, "MLP widths %d/%d/%d exceed shared memory", h1, h2, h3);
+    }
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(MGS_ERR_CUDA, "cannot select device %d", ctx->device);
 
@@ -437,7 +453,43 @@ mgs_status mgs_load_scene(mgs_ctx ctx, const mgs_scene_desc *d, mgs_stream strea
                             stream);
     }
     s->bytes = (int64_t)bytes;
-    if (e == cudaSuccess && all_mlp) {
+    if (e == cudaSuccess && all_mlp && wide) {
+        // pack: w1 [h1][32] (cols 22.. zero), w2 [h2][h1], w3 [h3][h2],
+        // w4 [8][h3] (rows 5.. zero), then FP32 b1 [h1], b2 [h2], b3 [h3], b4 [8]
+        const size_t n_w1 = (size_t)h1 * kMlpK1, n_w2 = (size_t)h2 * h1, n_w3 = (size_t)h3 * h2,
+                     n_w4 = (size_t)kMlpN3 * h3;
+        const size_t off_w2 = n_w1 * 2, off_w3 = off_w2 + n_w2 * 2, off_w4 = off_w3 + n_w3 * 2,
+                     off_b1 = (off_w4 + n_w4 * 2 + 15) / 16 * 16, off_b2 = off_b1 + h1 * 4,
+                     off_b3 = off_b2 + h2 * 4, off_b4 = off_b3 + h3 * 4, total = off_b4 + 8 * 4;
+        std::vector<unsigned char> blob(total, 0);
+        uint16_t *w1 = reinterpret_cast<uint16_t *>(blob.data());
+        for (int r = 0; r < h1; ++r)
+            for (int c = 0; c < kMlpIn; ++c) w1[r * kMlpK1 + c] = d->mlp_w1[r * kMlpIn + c];
+        memcpy(blob.data() + off_w2, d->mlp_w2, n_w2 * 2);
+        memcpy(blob.data() + off_w3, d->mlp_w3, n_w3 * 2);
+        memcpy(blob.data() + off_w4, d->mlp_w4, (size_t)kMlpOut * h3 * 2);
+        memcpy(blob.data() + off_b1, d->mlp_b1, h1 * 4);
+        memcpy(blob.data() + off_b2, d->mlp_b2, h2 * 4);
+        memcpy(blob.data() + off_b3, d->mlp_b3, h3 * 4);
+        memcpy(blob.data() + off_b4, d->mlp_b4, kMlpOut * 4);
+        e = cudaMalloc(&s->mlp_blob, total);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->mlp_blob, blob.data(), total, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        s->mlp.w1 = reinterpret_cast<const __nv_bfloat16 *>(s->mlp_blob);
+        s->mlp.w2 = reinterpret_cast<const __nv_bfloat16 *>(s->mlp_blob + off_w2);
+        s->mlp.w3 = reinterpret_cast<const __nv_bfloat16 *>(s->mlp_blob + off_w3);
+        s->mlp.w4 = reinterpret_cast<const __nv_bfloat16 *>(s->mlp_blob + off_w4);
+        s->mlp.b1 = reinterpret_cast<const float *>(s->mlp_blob + off_b1);
+        s->mlp.b2 = reinterpret_cast<const float *>(s->mlp_blob + off_b2);
+        s->mlp.b3 = reinterpret_cast<const float *>(s->mlp_blob + off_b3);
+        s->mlp.b4 = reinterpret_cast<const float *>(s->mlp_blob + off_b4);
+        s->mlp.h1 = h1;
+        s->mlp.h2 = h2;
+        s->mlp.h3 = h3;
+        s->has_mlp = true;
+        s->bytes += (int64_t)total;
+    } else if (e == cudaSuccess && all_mlp) {
         // pack: w1 [64][32] (cols 22.. zero), w2 [64][64], w3 [8][64] (rows 5.. zero)
         const size_t n_w1 = kMlpHidden * kMlpK1, n_w2 = kMlpHidden * kMlpHidden,
                      n_w3 = kMlpN3 * kMlpHidden;

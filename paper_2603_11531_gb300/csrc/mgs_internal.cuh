@@ -31,13 +31,49 @@ struct DevCamera {
 
 // Packed MLP weights in device memory (BF16, row-major [out][in], padded).
 struct DevMLP {
-    const __nv_bfloat16 *w1;  // [64][32]
-    const __nv_bfloat16 *w2;  // [64][64]
-    const __nv_bfloat16 *w3;  // [8][64]
-    const float *b1;          // [64]
-    const float *b2;          // [64]
-    const float *b3;          // [8]
+    const __nv_bfloat16 *w1;  // [64][32]        wide: [h1][32]
+    const __nv_bfloat16 *w2;  // [64][64]        wide: [h2][h1]
+    const __nv_bfloat16 *w3;  // [8][64] (head)  wide: [h3][h2]
+    const float *b1;          // [64]            wide: [h1]
+    const float *b2;          // [64]            wide: [h2]
+    const float *b3;          // [8]             wide: [h3]
+    const __nv_bfloat16 *w4;  // wide only: head [8][h3]
+    const float *b4;          // wide only: [8]
+    int h1, h2, h3;           // 0: the 22-64-64-5 MLP; else App. C's three hidden layers
 };
+
+// Shared-memory layout (byte offsets) of the wide (three hidden layer)
+// tcgen05 MLP for one 128-row tile: BF16 operands in canonical K-major
+// layout (x, activations a0/a1, weights w1..w3), the FP32 head and biases.
+struct WideLayout {
+    uint32_t x, a0, a1, w1, w2, w3, head, b1, b2, b3, b4, mbar, tmem, total;
+};
+__host__ __device__ inline WideLayout wide_layout(int h1, int h2, int h3) {
+    WideLayout L{};
+    uint32_t o = 0;
+    auto take = [&o](uint32_t bytes, uint32_t align) {
+        o = (o + align - 1) / align * align;
+        const uint32_t r = o;
+        o += bytes;
+        return r;
+    };
+    L.x = take(128u * 32u * 2u, 128u);
+    L.a0 = take(128u * (uint32_t)h1 * 2u, 128u);
+    L.a1 = take(128u * (uint32_t)h2 * 2u, 128u);
+    L.w1 = take((uint32_t)h1 * 32u * 2u, 128u);
+    L.w2 = take((uint32_t)h2 * (uint32_t)h1 * 2u, 128u);
+    L.w3 = take((uint32_t)h3 * (uint32_t)h2 * 2u, 128u);
+    L.head = take(5u * (uint32_t)h3 * 4u, 16u);
+    L.b1 = take((uint32_t)h1 * 4u, 16u);
+    L.b2 = take((uint32_t)h2 * 4u, 16u);
+    L.b3 = take((uint32_t)h3 * 4u, 16u);
+    L.b4 = take(8u * 4u, 16u);
+    L.mbar = take(8u, 8u);
+    L.tmem = take(4u, 4u);
+    L.total = o;
+    return L;
+}
+inline size_t wide_mlp_smem(int h1, int h2, int h3) { return wide_layout(h1, h2, h3).total; }
 
 // Device-visible status of a workspace (accumulates until the host syncs).
 constexpr unsigned kStatusOverflow = 1u;    // some render exceeded its pair capacity

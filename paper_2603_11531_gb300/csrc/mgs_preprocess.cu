@@ -175,10 +175,12 @@ __device__ __forceinline__ void camera_centre(const DevCamera &cam, float (&c)[3
 
 // kTC: the MLP runs on tcgen05 (TMEM accumulators, one CTA = 128 rows);
 // otherwise on mma.sync (one warp = 32 rows).
-template <bool kFP16, bool kMLP, bool kResidual, bool kTC>
-__global__ void __launch_bounds__(kTC ? tc::kThreads : kThreads)
+// kWide: the paper-width MLP (three hidden layers) on tcgen05, 128 rows per CTA.
+template <bool kFP16, bool kMLP, bool kResidual, bool kTC, bool kWide = false>
+__global__ void __launch_bounds__(kWide ? tcw::kThreads : (kTC ? tc::kThreads : kThreads))
     k_preprocess(RenderArgs args) {
-    constexpr int kStep = kTC ? tc::kThreads : kThreads;   // Gaussians per CTA step
+    constexpr int kStep =
+        kWide ? tcw::kThreads : (kTC ? tc::kThreads : kThreads);   // Gaussians per CTA step
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpSmem &sm = *reinterpret_cast<MlpSmem *>(smem_raw);
     tc::Smem &tsm = *reinterpret_cast<tc::Smem *>(smem_raw);
@@ -186,7 +188,11 @@ __global__ void __launch_bounds__(kTC ? tc::kThreads : kThreads)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t tc_phase = 0;
     bool tc_ok = true;
-    if constexpr (kMLP && kTC) {
+    WideLayout wl{};
+    if constexpr (kWide) {
+        wl = wide_layout(args.mlp.h1, args.mlp.h2, args.mlp.h3);
+        tcw::setup(smem_raw, wl, args.mlp);
+    } else if constexpr (kMLP && kTC) {
         tc::setup(tsm, args.mlp);
     } else if constexpr (kMLP) {
         mlp_load_weights(sm, args.mlp);
@@ -228,7 +234,11 @@ __global__ void __launch_bounds__(kTC ? tc::kThreads : kThreads)
                 for (int k = 0; k < 12; ++k) f[10 + k] = v[11 + k];
             }
             float o[5];
-            if constexpr (kTC) {
+            if constexpr (kWide) {
+                tcw::put_features(smem_raw, wl, f);
+                tc_ok &= tcw::mlp_cta(smem_raw, wl, args.mlp.h1, args.mlp.h2, args.mlp.h3,
+                                      tc_phase, o);
+            } else if constexpr (kTC) {
                 tc::put_features(tsm, f);
                 tc_ok &= tc::mlp_cta(tsm, tc_phase, o);
             } else {
@@ -292,10 +302,28 @@ __global__ void __launch_bounds__(kTC ? tc::kThreads : kThreads)
     for (int o = 16; o > 0; o >>= 1) wbound = fmaxf(wbound, __shfl_xor_sync(0xffffffffu, wbound, o));
     if ((threadIdx.x & 31) == 0 && wbound > 0.0f)
         atomicMax(&args.status->wmax_bits, __float_as_uint(wbound));
-    if constexpr (kMLP && kTC) {
+    if constexpr (kWide) {
+        tcw::teardown(smem_raw, wl);
+        if (!tc_ok && threadIdx.x == 0) atomicOr(&args.status->overflow, kStatusMmaTimeout);
+    } else if constexpr (kMLP && kTC) {
         tc::teardown(tsm);
         if (!tc_ok && threadIdx.x == 0) atomicOr(&args.status->overflow, kStatusMmaTimeout);
     }
+}
+
+template <bool kFP16, bool kResidual>
+cudaError_t launch_wide(const RenderArgs &a, int sm_count, cudaStream_t stream) {
+    const size_t smem = wide_mlp_smem(a.mlp.h1, a.mlp.h2, a.mlp.h3);
+    auto kern = k_preprocess<kFP16, true, kResidual, true, true>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // one CTA per SM (shared memory), each holding 256 TMEM columns
+    int64_t blocks = (a.n + tcw::kThreads - 1) / tcw::kThreads;
+    if (blocks > sm_count) blocks = sm_count;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, tcw::kThreads, smem, stream>>>(a);
+    return cudaGetLastError();
 }
 
 template <bool kFP16, bool kMLP, bool kResidual, bool kTC>
@@ -323,6 +351,13 @@ cudaError_t launch_t(const RenderArgs &a, int sm_count, cudaStream_t stream) {
 cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream) {
     const bool fp16 = a.precision == MGS_PREC_FP16;
     const bool sync_mma = (a.flags & MGS_FLAG_MLP_MMA_SYNC) != 0;
+    if (a.use_mlp && a.mlp.h1 != 0) {
+        if (a.rgb_residual)
+            return fp16 ? launch_wide<true, true>(a, sm_count, stream)
+                        : launch_wide<false, true>(a, sm_count, stream);
+        return fp16 ? launch_wide<true, false>(a, sm_count, stream)
+                    : launch_wide<false, false>(a, sm_count, stream);
+    }
     if (a.use_mlp) {
         if (sync_mma) {
             if (a.rgb_residual)

@@ -258,4 +258,169 @@ __device__ __forceinline__ bool mlp_cta(Smem &sm, uint32_t &phase, float (&out)[
 }
 
 }  // namespace tc
+
+// ---------------------------------------------------------------------------
+// The paper-width MLP_f (App. C: three hidden layers, e.g. 256, 128, 64):
+// one CTA of 128 threads evaluates 128 Gaussians per step; layer l is one
+// M = 128, N = h_l tcgen05 MMA chain (K = 16 per instruction) whose FP32
+// accumulator occupies TMEM columns 0 .. h_l - 1 (256 columns allocated);
+// thread t reads row t, adds the bias, applies ReLU, rounds to BF16 and
+// writes the next layer's A operand; the 5-wide head runs on CUDA cores.
+namespace tcw {
+
+constexpr int kThreads = 128;
+constexpr int kTmemCols = 256;
+
+__device__ __forceinline__ void put_bf16(unsigned char *base, uint32_t off, int row, int k, int K,
+                                         __nv_bfloat16 v) {
+    *reinterpret_cast<__nv_bfloat16 *>(base + off + tc::core_off(row, k, K)) = v;
+}
+
+__device__ __forceinline__ void setup(unsigned char *base, const WideLayout &L, const DevMLP &mlp) {
+    const int h1 = mlp.h1, h2 = mlp.h2, h3 = mlp.h3;
+    for (int e = threadIdx.x; e < h1 * kMlpK1; e += blockDim.x)
+        put_bf16(base, L.w1, e / kMlpK1, e % kMlpK1, kMlpK1, mlp.w1[e]);
+    for (int e = threadIdx.x; e < h2 * h1; e += blockDim.x)
+        put_bf16(base, L.w2, e / h1, e % h1, h1, mlp.w2[e]);
+    for (int e = threadIdx.x; e < h3 * h2; e += blockDim.x)
+        put_bf16(base, L.w3, e / h2, e % h2, h2, mlp.w3[e]);
+    float *head = reinterpret_cast<float *>(base + L.head);
+    for (int e = threadIdx.x; e < kMlpOut * h3; e += blockDim.x) head[e] = __bfloat162float(mlp.w4[e]);
+    float *b1 = reinterpret_cast<float *>(base + L.b1);
+    float *b2 = reinterpret_cast<float *>(base + L.b2);
+    float *b3 = reinterpret_cast<float *>(base + L.b3);
+    float *b4 = reinterpret_cast<float *>(base + L.b4);
+    for (int e = threadIdx.x; e < h1; e += blockDim.x) b1[e] = mlp.b1[e];
+    for (int e = threadIdx.x; e < h2; e += blockDim.x) b2[e] = mlp.b2[e];
+    for (int e = threadIdx.x; e < h3; e += blockDim.x) b3[e] = mlp.b3[e];
+    if (threadIdx.x < kMlpOut) b4[threadIdx.x] = mlp.b4[threadIdx.x];
+    const uint32_t mbar = tc::saddr(base + L.mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc::saddr(base + L.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+}
+
+__device__ __forceinline__ void teardown(unsigned char *base, const WideLayout &L) {
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x < 32) {
+        const uint32_t tmem = *reinterpret_cast<const uint32_t *>(base + L.tmem);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+// D[128 x N] (TMEM columns 0..N-1) = A[128 x K] B[N x K]^T, issued by thread 0.
+__device__ __forceinline__ bool layer(unsigned char *base, const WideLayout &L, uint32_t a_off,
+                                      uint32_t b_off, int K, int N, uint32_t &phase) {
+    const uint32_t tmem = *reinterpret_cast<const uint32_t *>(base + L.tmem);
+    const uint32_t mbar = tc::saddr(base + L.mbar);
+    if (threadIdx.x == 0) {
+        tc::fence_after();
+        const uint32_t sbo = (uint32_t)(K >> 3) << 7;
+        const uint32_t idesc = tc::idesc_bf16(128, N);
+        const uint32_t a0 = tc::saddr(base + a_off), b0 = tc::saddr(base + b_off);
+#pragma unroll 1
+        for (int s = 0; s < K / 16; ++s) {
+            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)s * 256u, 128u, sbo);
+            const uint64_t bd = tc::smem_desc(b0 + (uint32_t)s * 256u, 128u, sbo);
+            tc::mma(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+        }
+        tc::commit(mbar);
+    }
+    const bool ok = tc::wait(mbar, phase);
+    phase ^= 1u;
+    tc::fence_after();
+    return ok;
+}
+
+// BF16(ReLU(D + b)) of this thread's row into the next A operand (K = N).
+__device__ __forceinline__ void relu_to_bf16(unsigned char *base, const WideLayout &L,
+                                             uint32_t bias_off, uint32_t out_off, int N) {
+    const uint32_t tmem = *reinterpret_cast<const uint32_t *>(base + L.tmem);
+    const uint32_t lane0 = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);
+    const float *b = reinterpret_cast<const float *>(base + bias_off);
+    const int row = threadIdx.x;
+#pragma unroll 1
+    for (int c = 0; c < N; c += 16) {
+        float v[16];
+        tc::ld16(lane0 + (uint32_t)c, v);
+#pragma unroll
+        for (int i = 0; i < 16; i += 2)
+            tc::store_bf16x2(reinterpret_cast<__nv_bfloat16 *>(base + out_off),
+                             tc::core_off(row, c + i, N), fmaxf(v[i] + b[c + i], 0.0f),
+                             fmaxf(v[i + 1] + b[c + i + 1], 0.0f));
+    }
+}
+
+// Writes this thread's 32 features (row threadIdx.x) as BF16.
+__device__ __forceinline__ void put_features(unsigned char *base, const WideLayout &L,
+                                             const float (&f)[kMlpK1]) {
+#pragma unroll
+    for (int k = 0; k < kMlpK1; k += 2)
+        tc::store_bf16x2(reinterpret_cast<__nv_bfloat16 *>(base + L.x),
+                         tc::core_off(threadIdx.x, k, kMlpK1), f[k], f[k + 1]);
+}
+
+// The MLP of the CTA's 128 rows; out = (phi-logit, o-logit, d_r, d_g, d_b)
+// of this thread's row, biases added.  All threads call it.
+__device__ __forceinline__ bool mlp_cta(unsigned char *base, const WideLayout &L, int h1, int h2,
+                                        int h3, uint32_t &phase, float (&out)[5]) {
+    bool ok = true;
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    ok &= layer(base, L, L.x, L.w1, kMlpK1, h1, phase);
+    relu_to_bf16(base, L, L.b1, L.a0, h1);
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    ok &= layer(base, L, L.a0, L.w2, h1, h2, phase);
+    relu_to_bf16(base, L, L.b2, L.a1, h2);
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    ok &= layer(base, L, L.a1, L.w3, h2, h3, phase);
+    // third hidden layer: BF16(ReLU(.)) in registers, then the head
+    const uint32_t tmem = *reinterpret_cast<const uint32_t *>(base + L.tmem);
+    const uint32_t lane0 = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);
+    const float *b3 = reinterpret_cast<const float *>(base + L.b3);
+    const float *head = reinterpret_cast<const float *>(base + L.head);
+    const float *b4 = reinterpret_cast<const float *>(base + L.b4);
+    float acc[kMlpOut];
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) acc[k] = b4[k];
+#pragma unroll 1
+    for (int c = 0; c < h3; c += 16) {
+        float v[16];
+        tc::ld16(lane0 + (uint32_t)c, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(v[i] + b3[c + i], 0.0f)));
+#pragma unroll
+            for (int k = 0; k < kMlpOut; ++k) acc[k] = fmaf(head[k * h3 + c + i], h, acc[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) out[k] = acc[k];
+    tc::fence_before();
+    __syncthreads();
+    return ok;
+}
+
+}  // namespace tcw
 }  // namespace mgs
