@@ -89,6 +89,10 @@ def lib():
             L.orc_rasterize.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int,
                                         ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                         P, P, P]
+            L.orc_decode_sh.restype = None
+            L.orc_decode_sh.argtypes = [ctypes.c_int64, P, P, P, P]
+            L.orc_half_to_double.restype = ctypes.c_double
+            L.orc_half_to_double.argtypes = [ctypes.c_uint16]
             L.orc_rasterize_depth.restype = ctypes.c_int
             L.orc_rasterize_depth.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
@@ -227,6 +231,34 @@ def render_depth(attrs, cam, mlp=None, use_mlp=False, rgb_residual=False, tile_r
     offsets, gids = bin_tiles(g, cam.width, cam.height)
     return dict(gauss=g, offsets=offsets, gids=gids,
                 depth=rasterize_depth(g, offsets, gids, cam.width, cam.height, tile_range))
+
+
+class _SHMLP(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("w2", ctypes.c_void_p),
+                ("b2", ctypes.c_void_p), ("n_out", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def decode_sh(h, mlp_d, mlp_v) -> np.ndarray:
+    """Eq. 6 load-time decode: h (n, 6) = (h_d, h_v) -> SH coefficients (n, 12),
+    [f_d (Y0 rgb), f_v (Y1 rgb, Y2 rgb, Y3 rgb)].  mlp_*: objects with w1, b1,
+    w2, b2 as binary16 bit patterns (uint16)."""
+    h = np.ascontiguousarray(h, np.float64).reshape(-1, 6)
+    keep, structs = [], []
+    for m, n_out in ((mlp_d, 3), (mlp_v, 9)):
+        arrs = [np.ascontiguousarray(getattr(m, k), np.uint16) for k in ("w1", "b1", "w2", "b2")]
+        assert arrs[0].shape == (64, 6) and arrs[1].shape == (64,)
+        assert arrs[2].shape == (n_out, 64) and arrs[3].shape == (n_out,)
+        keep += arrs
+        structs.append(_SHMLP(*[a.ctypes.data for a in arrs], n_out, 0))
+    Y = np.zeros((len(h), 12), np.float64)
+    if len(h):
+        lib().orc_decode_sh(len(h), _ptr(h), ctypes.byref(structs[0]), ctypes.byref(structs[1]),
+                            _ptr(Y))
+    return Y
+
+
+def half_to_double(bits: int) -> float:
+    return lib().orc_half_to_double(int(bits))
 
 
 def rotation(q) -> np.ndarray:

@@ -575,3 +575,45 @@ int orc_rasterize_sorted(int64_t n, const orc_gauss *g, const int64_t *offsets,
     free(list);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 3.2, Eq. 6: SH features decoded once at load time                     */
+/* ------------------------------------------------------------------------- */
+
+/* IEEE binary16: 1 sign bit, 5 exponent bits (bias 15), 10 fraction bits. */
+double orc_half_to_double(uint16_t b)
+{
+    const int sign = (b >> 15) & 1, e = (b >> 10) & 31, f = b & 1023;
+    double v;
+    if (e == 0)
+        v = ldexp((double)f, -24);                 /* subnormal: f * 2^-14 / 2^10 */
+    else if (e == 31)
+        v = f ? NAN : INFINITY;
+    else
+        v = ldexp(1.0 + f / 1024.0, e - 15);
+    return sign ? -v : v;
+}
+
+static void sh_mlp_eval(const orc_sh_mlp *m, const double in[6], double *out)
+{
+    double hid[64];
+    for (int j = 0; j < 64; ++j) {
+        double acc = orc_half_to_double(m->b1[j]);
+        for (int i = 0; i < 6; ++i) acc += orc_half_to_double(m->w1[j * 6 + i]) * in[i];
+        hid[j] = acc > 0.0 ? acc : 0.0;
+    }
+    for (int k = 0; k < m->n_out; ++k) {
+        double acc = orc_half_to_double(m->b2[k]);
+        for (int j = 0; j < 64; ++j) acc += orc_half_to_double(m->w2[k * 64 + j]) * hid[j];
+        out[k] = acc;
+    }
+}
+
+void orc_decode_sh(int64_t n, const double *h, const orc_sh_mlp *mlp_d,
+                   const orc_sh_mlp *mlp_v, double *Y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        sh_mlp_eval(mlp_d, h + 6 * i, Y + 12 * i);       /* f_d -> Y0 rgb */
+        sh_mlp_eval(mlp_v, h + 6 * i, Y + 12 * i + 3);   /* f_v -> Y1..Y3 rgb */
+    }
+}

@@ -87,6 +87,25 @@ int64_t orc_gauss_size(void);
 /* Rotation matrix (row-major) of the normalised quaternion q = (w, x, y, z). */
 void orc_rotation(const double q[4], double R[9]);
 
+/* Load-time SH decode of Sec. 3.2, Eq. 6: f_d = MLP_d(h_d, h_v) (3 values,
+ * the degree-0 colour coefficients) and f_v = MLP_v(h_d, h_v) (9 values, the
+ * degree-1 coefficients Y1 rgb, Y2 rgb, Y3 rgb).  Each MLP has one hidden
+ * layer of 64 ReLU units (App. C) and 16-bit parameters: w1 [64][6],
+ * b1 [64], w2 [n_out][64], b2 [n_out] as IEEE binary16 bit patterns. */
+typedef struct {
+    const uint16_t *w1, *b1, *w2, *b2;
+    int32_t n_out;
+    int32_t pad;
+} orc_sh_mlp;
+
+/* h: n x 6 (h_d, h_v); Y: n x 12 SH coefficients, coefficient-major
+ * (Y0 rgb = f_d, then f_v). */
+void orc_decode_sh(int64_t n, const double *h, const orc_sh_mlp *mlp_d,
+                   const orc_sh_mlp *mlp_v, double *Y);
+
+/* Value of an IEEE binary16 bit pattern. */
+double orc_half_to_double(uint16_t b);
+
 /* Round to the nearest bfloat16 value, ties to even. */
 double orc_bf16_round(double v);
 

@@ -193,6 +193,41 @@ def random_mlp(seed: int, hidden=(MLP_HIDDEN, MLP_HIDDEN)) -> MLPWeights:
     return MLPWeights(w1, b1, w2, b2, w3, b3, w4, head_b)
 
 
+@dataclasses.dataclass
+class SHDecodeMLP:
+    """One load-time SH decoder of Eq. 6: 6 -> 64 (ReLU) -> n_out, all
+    parameters as IEEE binary16 bit patterns (uint16), row-major [out][in]."""
+    w1: np.ndarray   # (64, 6)
+    b1: np.ndarray   # (64,)
+    w2: np.ndarray   # (n_out, 64)
+    b2: np.ndarray   # (n_out,)
+
+
+def random_sh_decoders(seed: int):
+    """(MLP_d with 3 outputs, MLP_v with 9 outputs): Kaiming-uniform FP16
+    weights, small FP16 biases."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def mk(n_out):
+        b1 = math.sqrt(6.0 / 6)
+        w1 = rng.uniform(-b1, b1, size=(64, 6)).astype(np.float16).view(np.uint16)
+        bb1 = rng.uniform(-0.1, 0.1, size=64).astype(np.float16).view(np.uint16)
+        b2 = math.sqrt(6.0 / 64) * 0.5
+        w2 = rng.uniform(-b2, b2, size=(n_out, 64)).astype(np.float16).view(np.uint16)
+        bb2 = rng.uniform(-0.1, 0.1, size=n_out).astype(np.float16).view(np.uint16)
+        return SHDecodeMLP(w1, bb1, w2, bb2)
+
+    return mk(3), mk(9)
+
+
+def compressed_sh_features(n: int, seed: int, precision: str = "fp16") -> np.ndarray:
+    """Per-Gaussian (h_d, h_v) of Eq. 6 as stored after dequantisation:
+    N(0, 0.5) values, (n, 6)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = rng.normal(0.0, 0.5, size=(n, 6)).astype(np.float32)
+    return h.astype(np.float16) if precision == "fp16" else h
+
+
 PAPER_MLP_HIDDEN = (256, 128, 64)   # App. C: MLP_f widths
 
 
