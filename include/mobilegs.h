@@ -210,6 +210,29 @@ mgs_status mgs_render_depth(mgs_workspace ws, mgs_scene scene,
                             const mgs_camera *cam, const mgs_render_opts *opts,
                             float *out_rgb, float *out_depth, mgs_stream stream);
 
+/* Load-time SH decoder of Sec. 3.2, Eq. 6 (one of MLP_d, MLP_v): 6 inputs
+ * (h_d, h_v) -> 64 ReLU units -> n_out outputs (3 for MLP_d, 9 for MLP_v),
+ * every parameter an IEEE binary16 bit pattern (App. C: 16-bit MLPs),
+ * row-major [out][in].  Host pointers, read during the call. */
+typedef struct {
+    const uint16_t *w1;   /* [64][6] */
+    const uint16_t *b1;   /* [64] */
+    const uint16_t *w2;   /* [n_out][64] */
+    const uint16_t *b2;   /* [n_out] */
+} mgs_sh_mlp;
+
+/* Decodes the SH coefficients of n Gaussians once, before loading (Eq. 6):
+ * f_d = MLP_d(h_d, h_v) is written to attribute columns 11..13 (Y0 rgb) and
+ * f_v = MLP_v(h_d, h_v) to columns 14..22 (Y1 rgb, Y2 rgb, Y3 rgb) of the
+ * device array attrs (n x 24 elements of `precision`, other columns left
+ * untouched); h is a device array of n x 6 elements of `precision`.  FP32
+ * accumulation; FP16 attributes receive the result rounded to nearest.
+ * Asynchronous on `stream`; MGS_ERR_INVALID_ARG for NULL or bad arguments. */
+mgs_status mgs_decode_sh(mgs_ctx ctx, int64_t n, int32_t precision,
+                         const void *h, const mgs_sh_mlp *mlp_d,
+                         const mgs_sh_mlp *mlp_v, void *attrs,
+                         mgs_stream stream);
+
 /* End-to-end render into HOST memory: renders into a workspace-owned device
  * image and copies it to host_rgb (height x width x 3 FP32; pinned memory
  * gives an asynchronous copy).  Asynchronous on `stream` like mgs_render. */

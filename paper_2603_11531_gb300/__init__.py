@@ -41,7 +41,7 @@ EXPORTS = (
     "mgs_workspace_reserve", "mgs_workspace_bytes", "mgs_workspace_sync", "mgs_render",
     "mgs_render_checked", "mgs_render_to_host", "mgs_tile_lists", "mgs_last_error",
     "mgs_version", "mgs_workspace_set_timing", "mgs_workspace_stage_times",
-    "mgs_render_static", "mgs_render_backward", "mgs_render_depth",
+    "mgs_render_static", "mgs_render_backward", "mgs_render_depth", "mgs_decode_sh",
     "mgs_server_create", "mgs_server_destroy", "mgs_server_submit", "mgs_server_wait",
     "mgs_server_ticket", "mgs_server_stats", "mgs_now",
 )
@@ -75,6 +75,11 @@ class mgs_scene_desc(ctypes.Structure):
                 ("mlp_w3", ctypes.c_void_p), ("mlp_b3", ctypes.c_void_p),
                 ("mlp_w4", ctypes.c_void_p), ("mlp_b4", ctypes.c_void_p),
                 ("mlp_hidden", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32)]
+
+
+class mgs_sh_mlp(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p),
+                ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p)]
 
 
 def lib():
@@ -115,6 +120,8 @@ def lib():
                                        ctypes.POINTER(mgs_render_opts), P, P], I32),
                 "mgs_render_backward": ([P, P, ctypes.POINTER(mgs_camera),
                                          ctypes.POINTER(mgs_render_opts), P, P, P, P, P], I32),
+                "mgs_decode_sh": ([P, I64, I32, P, ctypes.POINTER(mgs_sh_mlp),
+                                   ctypes.POINTER(mgs_sh_mlp), P, P], I32),
                 "mgs_last_error": ([], ctypes.c_char_p),
                 "mgs_version": ([], ctypes.c_char_p),
             }
@@ -282,6 +289,29 @@ def mgs_render_depth(ws, scene, cam, opts, out_rgb, out_depth, stream=None):
     c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
     _check(lib().mgs_render_depth(ws, scene, ctypes.byref(c), ctypes.byref(opts), _ptr(out_rgb),
                                   _ptr(out_depth), _stream(stream)))
+
+
+def mgs_decode_sh(ctx, h, mlp_d, mlp_v, attrs, stream=None):
+    """Eq. 6 load-time SH decode into columns 11..22 of the device tensor
+    attrs (N, 24); h: device tensor (N, 6) of the same dtype; mlp_*: objects
+    with w1, b1, w2, b2 as binary16 bit patterns."""
+    import torch
+    if attrs.dtype != h.dtype or attrs.dtype not in (torch.float16, torch.float32):
+        raise TypeError("h and attrs must both be float16 or float32")
+    if not (attrs.is_cuda and h.is_cuda and attrs.is_contiguous() and h.is_contiguous()):
+        raise ValueError("h and attrs must be contiguous CUDA tensors")
+    if h.shape[1] != 6 or attrs.shape[1] != 24 or h.shape[0] != attrs.shape[0]:
+        raise ValueError("h must be (N, 6) and attrs (N, 24)")
+    keep, ss = [], []
+    for m, n_out in ((mlp_d, 3), (mlp_v, 9)):
+        arrs = [np.ascontiguousarray(getattr(m, k), np.uint16) for k in ("w1", "b1", "w2", "b2")]
+        if arrs[0].shape != (64, 6) or arrs[2].shape != (n_out, 64):
+            raise ValueError("SH decoder shapes: w1 (64, 6), w2 (%d, 64)" % n_out)
+        keep += arrs
+        ss.append(mgs_sh_mlp(*[a.ctypes.data for a in arrs]))
+    prec = MGS_PREC_FP16 if attrs.dtype == torch.float16 else MGS_PREC_FP32
+    _check(lib().mgs_decode_sh(ctx, int(h.shape[0]), prec, _ptr(h), ctypes.byref(ss[0]),
+                               ctypes.byref(ss[1]), _ptr(attrs), _stream(stream)))
 
 
 def mgs_render_to_host(ws, scene, cam, opts, host_rgb, stream=None):
