@@ -215,28 +215,34 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
     }
 }
 
-// One CTA per tile, longest tile lists first.
 // ---------------------------------------------------------------------------
 // Tensor-core accumulation of A and B (FP16-attribute scenes).
 //
 // One CTA (four warps) per tile; warp w owns the 16x4 block of rows
-// 4w..4w+3.  A warp's 64 pixels are the M = 64 rows of four m16n8k16 tiles:
+// 4w..4w+3.  A warp's 64 pixels are the M = 64 rows of four m16n8k8 tiles:
 // lane (g, t) = (lane / 4, lane % 4) owns the eight pixels
 // x = 8 (g / 4) + 0..7 of row g % 4 (rows g and g + 8 of m-tile i are
 // pixels 2i and 2i + 1), shared by the four lanes of its quad.  Candidates
-// are gathered into chunks of 16 Gaussians (the K dimension); lane t of a
-// quad evaluates chunk entries 2t, 2t + 1, 2t + 8, 2t + 9 at its pixels, which
-// is exactly the A fragment it holds.  B = the chunk's weights
-// [-w c_r, -w c_g, -w c_b, -w] as FP16 high parts (columns 0-3) and low
-// parts (columns 4-7), so column c + column c + 4 is the sum with a 22-bit
-// weight.  Weights are scaled by a power of two when the frame's largest
-// weight would overflow FP16 (the scale cancels in A / B and is divided out).
+// are gathered into chunks of 8 Gaussians (the K dimension); lane t of a
+// quad evaluates chunk entries 2t and 2t + 1 at its pixels -- one packed
+// FP32x2 operation serves both, and the packed pair of alphas is exactly the
+// A fragment the lane holds.  B = the chunk's weights [w c_r, w c_g, w c_b, w]
+// as FP16 high parts (columns 0-3) and low parts (columns 4-7), so column c +
+// column c + 4 is the sum with a 22-bit weight.  Weights are scaled by a
+// power of two when the frame's largest weight would overflow FP16 (the
+// scale cancels in A / B and is divided out).  T stays in FP32 FMAs.
 constexpr int kTcThreads = 128;
 constexpr int kTcWarps = kTcThreads / 32;
-constexpr int kRing = 48;        // candidate slots per warp: three chunks of 16
+constexpr int kChunk = 8;        // candidates per MMA (K)
+constexpr int kRing = 40;        // candidate slots per warp: five chunks
 
+// Ring slot s stores its geometry in pair-interleaved words, so that lane t
+// reads the two entries 2t, 2t + 1 of a chunk with one 16-byte load each:
+//   geo[0][s / 2] = {m_x(a), m_x(b), m_y(a), m_y(b)}
+//   geo[1][s / 2] = {l11(a), l11(b), l21(a), l21(b)}
+//   geo[2][s / 2] = {l22(a), l22(b), log2 o(a), log2 o(b)}   (a = even slot)
 struct TcSmem {
-    ulonglong2 geo[kTcWarps][3][kRing];   // duplicated pairs as in accumulate()
+    float4 geo[kTcWarps][3][kRing / 2];
     __half wt[kTcWarps][8][kRing];        // weight column c of slot s (FP16)
 };
 
@@ -245,70 +251,55 @@ __device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                        uint32_t b1) {
+__device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
+        "mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+        "{%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        : "r"(a0), "r"(a1), "r"(b0));
 }
 
-// Negated, clamped alpha of ring slot s at the lane's eight pixels (pairs of
-// pixels 2i, 2i + 1), the same FP32 sequence as accumulate(); T updated.
-template <bool kCount>
-__device__ __forceinline__ void tc_alpha(const ulonglong2 (*geo)[kRing], int s, const f2 (&pxc)[4],
-                                         f2 pyc, f2 kq2, f2 (&T)[4], f2 (&n)[4], int (&cnt)[8]) {
-    const ulonglong2 s0 = geo[0][s], s1 = geo[1][s], s2 = geo[2][s];
-    const f2 dy = sub2(pyc, s0.y);
-    const f2 ldy = mul2(s1.y, dy);
-    const f2 e2 = mul2(s2.x, dy);
+// One chunk of 8 candidates starting at ring slot c0 (a multiple of 8): the
+// lane's entries 2t, 2t + 1 at its eight pixels (same FP32 sequence as
+// accumulate()), T updated, alphas packed to FP16 and summed by four MMAs.
+template <bool kCount, bool kClamp>
+__device__ __forceinline__ void tc_chunk(const float4 (*geo)[kRing / 2], const __half (*wt)[kRing],
+                                         int c0, int g, int t, const f2 (&pxc)[8], f2 pyc,
+                                         f2 kq2, float (&T)[8], float (&D)[4][4], int (&cnt)[8]) {
+    const int pr = (c0 >> 1) + t;
+    const float4 q0 = geo[0][pr], q1 = geo[1][pr], q2 = geo[2][pr];
+    const f2 mx = pk(q0.x, q0.y), my = pk(q0.z, q0.w);
+    const f2 l11 = pk(q1.x, q1.y), l21 = pk(q1.z, q1.w);
+    const f2 l22 = pk(q2.x, q2.y), lo = pk(q2.z, q2.w);
+    const f2 dy = sub2(pyc, my);
+    const f2 ldy = mul2(l21, dy);
+    const f2 e2 = mul2(l22, dy);
     const f2 e2s = mul2(e2, e2);
+    uint32_t a[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const f2 dx = sub2(pxc[i], s0.x);
-        const f2 e1 = fma2(s1.x, dx, ldy);
+    for (int j = 0; j < 8; ++j) {
+        const f2 dx = sub2(pxc[j], mx);
+        const f2 e1 = fma2(l11, dx, ldy);
         const f2 q = fma2(e1, e1, e2s);
-        const f2 g = fma2(q, kq2, s2.y);
-        float q0, q1, g0, g1;
-        upk(q, q0, q1);
-        upk(g, g0, g1);
-        const float n0 = q0 <= 9.0f ? fmaxf(-ex2(g0), -0.99f) : 0.0f;
-        const float n1 = q1 <= 9.0f ? fmaxf(-ex2(g1), -0.99f) : 0.0f;
-        if (kCount) {
-            cnt[2 * i] += q0 <= 9.0f;
-            cnt[2 * i + 1] += q1 <= 9.0f;
+        const f2 gg = fma2(q, kq2, lo);
+        float qa, qb, ga, gb;
+        upk(q, qa, qb);
+        upk(gg, ga, gb);
+        float aa = ex2(ga), ab = ex2(gb);
+        if (kClamp) {
+            aa = fminf(aa, 0.99f);
+            ab = fminf(ab, 0.99f);
         }
-        n[i] = pk(n0, n1);
-        T[i] = fma2(n[i], T[i], T[i]);
+        aa = qa <= 9.0f ? aa : 0.0f;
+        ab = qb <= 9.0f ? ab : 0.0f;
+        if (kCount) cnt[j] += (qa <= 9.0f) + (qb <= 9.0f);
+        T[j] = fmaf(-aa, T[j], T[j]);
+        T[j] = fmaf(-ab, T[j], T[j]);
+        a[j] = h2bits(aa, ab);            // k = 2t (low half), 2t + 1
     }
-}
-
-// One chunk of 16 candidates starting at ring slot c0 (a multiple of 16).
-template <bool kCount>
-__device__ __forceinline__ void tc_chunk(const ulonglong2 (*geo)[kRing], const __half (*wt)[kRing],
-                                         int c0, int g, int t, const f2 (&pxc)[4], f2 pyc, f2 kq2,
-                                         f2 (&T)[4], float (&D)[4][4], int (&cnt)[8]) {
-    uint32_t a[4][4];
+    const uint32_t b0 = reinterpret_cast<const uint32_t *>(wt[g])[(c0 >> 1) + t];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        f2 na[4], nb[4];
-        tc_alpha<kCount>(geo, c0 + 2 * t + 8 * p, pxc, pyc, kq2, T, na, cnt);
-        tc_alpha<kCount>(geo, c0 + 2 * t + 8 * p + 1, pxc, pyc, kq2, T, nb, cnt);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float a0, a1, b0, b1;
-            upk(na[i], a0, a1);
-            upk(nb[i], b0, b1);
-            a[i][2 * p] = h2bits(a0, b0);      // pixel 2i (row g): k = 2t (+8p), 2t + 1 (+8p)
-            a[i][2 * p + 1] = h2bits(a1, b1);  // pixel 2i + 1 (row g + 8)
-        }
-    }
-    const uint32_t *col = reinterpret_cast<const uint32_t *>(wt[g]);
-    const uint32_t b0 = col[(c0 >> 1) + t];      // k = 2t, 2t + 1 of column g
-    const uint32_t b1 = col[(c0 >> 1) + 4 + t];  // k = 2t + 8, 2t + 9
-#pragma unroll
-    for (int i = 0; i < 4; ++i) mma_f16(D[i], a[i], b0, b1);
+    for (int i = 0; i < 4; ++i) mma_k8(D[i], a[2 * i], a[2 * i + 1], b0);   // pixels 2i, 2i + 1
 }
 
 template <bool kAux, bool kCount>
@@ -320,7 +311,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     const int bx0 = tx * kTile, by0 = ty * kTile + 4 * warp;
     const int xb = bx0 + 8 * (g >> 2);
     const int py = by0 + (g & 3);
-    const ulonglong2(*geo)[kRing] = sm.geo[warp];
+    float4(*geo)[kRing / 2] = sm.geo[warp];
     __half(*wt)[kRing] = sm.wt[warp];
 
     const uint32_t start = args.tile_offsets[tile];
@@ -330,49 +321,67 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     // weight scale 2^(14 - e) when the frame's largest weight has exponent e >= 14
     const int we = (int)((args.status->wmax_frame_bits >> 23) & 0xFFu) - 127;
     const float wscale = we >= 14 ? __int_as_float((127 + 14 - we) << 23) : 1.0f;
+    const float kLogClamp = -0.014499569695115089f;   // log2(0.99)
 
-    f2 pxc[4];
+    f2 pxc[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) pxc[i] = pk((float)(xb + 2 * i) + 0.5f, (float)(xb + 2 * i) + 1.5f);
+    for (int j = 0; j < 8; ++j) pxc[j] = pk((float)(xb + j) + 0.5f, (float)(xb + j) + 0.5f);
     const f2 pyc = pk((float)py + 0.5f, (float)py + 0.5f);
     const float kq = -0.72134752044448170f;  // -log2(e) / 2
     const f2 kq2 = pk(kq, kq);
-    f2 T[4];
+    float T[8];
     float D[4][4];
     int cnt[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        T[i] = pk(1.0f, 1.0f);
-        D[i][0] = D[i][1] = D[i][2] = D[i][3] = 0.0f;
-        cnt[2 * i] = cnt[2 * i + 1] = 0;
+    for (int j = 0; j < 8; ++j) {
+        T[j] = 1.0f;
+        cnt[j] = 0;
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) D[i][0] = D[i][1] = D[i][2] = D[i][3] = 0.0f;
 
-    int head = 0, count = 0;   // unprocessed candidates: ring slots [head, head + count)
-    float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f), b_n = a_n, c_n = a_n;
+    int head = 0, count = 0;          // unprocessed candidates: ring slots [head, head + count)
+    uint64_t clamp_mask = 0;          // ring slots whose opacity exceeds 0.99
+    // prefetch of the next batch: the fields the block test needs
+    float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f);
+    float l22_n = 0.f;
+    uint32_t gid_n = 0;
     if (start + lane < end) {
-        const uint32_t gid = __ldg(&args.gids[start + lane]);
-        a_n = __ldg(&args.rec[gid].a);
-        b_n = __ldg(&args.rec[gid].b);
-        c_n = __ldg(&args.rec[gid].c);
+        gid_n = __ldg(&args.gids[start + lane]);
+        a_n = __ldg(&args.rec[gid_n].a);
+        l22_n = __ldg(&args.rec[gid_n].b.x);
     }
     for (uint32_t base = start; base < end; base += 32) {
         const uint32_t j = base + lane;
-        const float4 a = a_n, b = b_n, c = c_n;
+        const float4 a = a_n;
+        const float l22 = l22_n;
+        const uint32_t gid = gid_n;
         const bool cand =
-            j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bcx, bcy, 7.5f, 1.5f));
+            j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, l22, bcx, bcy, 7.5f, 1.5f));
         if (j + 32 < end) {
-            const uint32_t gid = __ldg(&args.gids[j + 32]);
-            a_n = __ldg(&args.rec[gid].a);
-            b_n = __ldg(&args.rec[gid].b);
-            c_n = __ldg(&args.rec[gid].c);
+            gid_n = __ldg(&args.gids[j + 32]);
+            a_n = __ldg(&args.rec[gid_n].a);
+            l22_n = __ldg(&args.rec[gid_n].b.x);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        bool clamp = false;
+        int pos = 0;
         if (cand) {
-            const int pos = (head + count + __popc(bal & ((1u << lane) - 1u))) % kRing;
-            sm.geo[warp][0][pos] = make_ulonglong2(pk(a.x, a.x), pk(a.y, a.y));
-            sm.geo[warp][1][pos] = make_ulonglong2(pk(a.z, a.z), pk(a.w, a.w));
-            sm.geo[warp][2][pos] = make_ulonglong2(pk(b.x, b.x), pk(b.y, b.y));
-            const float w4[4] = {b.w * wscale, c.x * wscale, c.y * wscale, b.z * wscale};
+            pos = (head + count + __popc(bal & ((1u << lane) - 1u))) % kRing;
+            const float4 b = __ldg(&args.rec[gid].b);
+            const float2 c = __ldg(reinterpret_cast<const float2 *>(&args.rec[gid].c));
+            float *q = reinterpret_cast<float *>(&geo[0][pos >> 1]);
+            const int o = pos & 1;
+            q[o] = a.x;
+            q[2 + o] = a.y;
+            q = reinterpret_cast<float *>(&geo[1][pos >> 1]);
+            q[o] = a.z;
+            q[2 + o] = a.w;
+            q = reinterpret_cast<float *>(&geo[2][pos >> 1]);
+            q[o] = b.x;
+            q[2 + o] = b.y;
+            clamp = b.y > kLogClamp;
+            const float w4[4] = {-b.w * wscale, -c.x * wscale, -c.y * wscale, -b.z * wscale};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const __half hi = __float2half_rn(w4[k]);
@@ -380,28 +389,50 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
                 wt[k + 4][pos] = __float2half_rn(w4[k] - __half2float(hi));
             }
         }
+        // slots of this batch that need the 0.99 clamp
+        const unsigned cb = __ballot_sync(0xffffffffu, clamp);
+        if (cb) {
+            for (unsigned m = cb; m; m &= m - 1) {
+                const int l = __ffs(m) - 1;
+                const int p = __shfl_sync(0xffffffffu, pos, l);
+                clamp_mask |= 1ull << p;
+            }
+        }
         __syncwarp();
         count += __popc(bal);
-        while (count >= 16) {
-            tc_chunk<kCount>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
-            head = head + 16 == kRing ? 0 : head + 16;
-            count -= 16;
+        while (count >= kChunk) {
+            if ((clamp_mask >> head) & 0xFFull)
+                tc_chunk<kCount, true>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+            else
+                tc_chunk<kCount, false>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+            clamp_mask &= ~(0xFFull << head);
+            head = head + kChunk == kRing ? 0 : head + kChunk;
+            count -= kChunk;
         }
         __syncwarp();
     }
     if (count > 0) {
         // pad the last chunk with entries that include no pixel and weigh 0
-        if (lane < 16 - count) {
+        if (lane < kChunk - count) {
             const int pos = (head + count + lane) % kRing;
-            const float far = 1e30f;
-            sm.geo[warp][0][pos] = make_ulonglong2(pk(far, far), pk(far, far));
-            sm.geo[warp][1][pos] = make_ulonglong2(pk(1.0f, 1.0f), 0ull);
-            sm.geo[warp][2][pos] = make_ulonglong2(pk(1.0f, 1.0f), 0ull);
+            const int o = pos & 1;
+            float *q = reinterpret_cast<float *>(&geo[0][pos >> 1]);
+            q[o] = 1e30f;
+            q[2 + o] = 1e30f;
+            q = reinterpret_cast<float *>(&geo[1][pos >> 1]);
+            q[o] = 1.0f;
+            q[2 + o] = 0.0f;
+            q = reinterpret_cast<float *>(&geo[2][pos >> 1]);
+            q[o] = 1.0f;
+            q[2 + o] = 0.0f;
 #pragma unroll
             for (int k = 0; k < 8; ++k) wt[k][pos] = __float2half_rn(0.0f);
         }
         __syncwarp();
-        tc_chunk<kCount>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+        if ((clamp_mask >> head) & 0xFFull)
+            tc_chunk<kCount, true>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+        else
+            tc_chunk<kCount, false>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
     }
 
     // Quad reduction: columns c and c + 4 (lanes t, t ^ 2), then swap halves
@@ -416,15 +447,10 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int k = 0; k < 4; ++k) o[i][k] = __shfl_xor_sync(0xffffffffu, v[i][k], 1);
-    float tt[8];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        upk(T[i], tt[2 * i], tt[2 * i + 1]);
-    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        tt[k] *= __shfl_xor_sync(0xffffffffu, tt[k], 1);
-        tt[k] *= __shfl_xor_sync(0xffffffffu, tt[k], 2);
+        T[k] *= __shfl_xor_sync(0xffffffffu, T[k], 1);
+        T[k] *= __shfl_xor_sync(0xffffffffu, T[k], 2);
         if (kCount) {
             cnt[k] += __shfl_xor_sync(0xffffffffu, cnt[k], 1);
             cnt[k] += __shfl_xor_sync(0xffffffffu, cnt[k], 2);
@@ -446,7 +472,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             const float ag = (even ? v[i][2 * h + 1] : o[i][2 * h + 1]) * inv;
             const float ab = (even ? o[i][2 * h] : v[i][2 * h]) * inv;
             const float bb = (even ? o[i][2 * h + 1] : v[i][2 * h + 1]) * inv;
-            const float tr = tt[2 * i + h];
+            const float tr = T[2 * i + h];
             const int64_t p = (int64_t)py * cam.width + x;
             const float fg = bb > 0.0f ? (1.0f - tr) / bb : 0.0f;
             float *out = args.out_rgb + 3 * p;
@@ -471,6 +497,7 @@ __host__ __device__ __forceinline__ bool use_tc(const RenderArgs &a) {
     return a.precision == MGS_PREC_FP16 && (a.flags & MGS_FLAG_RASTER_FMA) == 0;
 }
 
+// One CTA per tile, longest tile lists first.
 template <bool kAux, bool kCount, bool kDepth = false>
 __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
     __shared__ ulonglong2 buf[kWarps][kDepth ? 6 : 5][32];
