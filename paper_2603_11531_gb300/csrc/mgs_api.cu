@@ -87,6 +87,7 @@ struct mgs_workspace_s {
     uint64_t pair_cap = 0;
     int64_t img_cap = 0;
     ProjRec *rec = nullptr;
+    uint4 *wt16 = nullptr;
     uint2 *rect = nullptr;
     uint32_t *tile_count = nullptr;
     uint32_t *tile_offsets = nullptr;
@@ -112,7 +113,7 @@ struct mgs_workspace_s {
 namespace {
 
 int64_t ws_bytes(const mgs_workspace_s *w) {
-    return w->n_cap * (int64_t)(sizeof(ProjRec) + sizeof(uint2)) +
+    return w->n_cap * (int64_t)(sizeof(ProjRec) + sizeof(uint2) + sizeof(uint4)) +
            w->tiles_cap * 3 * (int64_t)sizeof(uint32_t) + (int64_t)w->pair_cap * 4 +
            w->img_cap * 12 + w->bases_cap * 4 + (int64_t)sizeof(DevStatus);
 }
@@ -122,9 +123,11 @@ mgs_status ws_ensure(mgs_workspace_s *w, int64_t n, int64_t tiles, uint64_t pair
     if (n > w->n_cap) {
         dev_free(w->rec);
         dev_free(w->rect);
+        dev_free(w->wt16);
         w->n_cap = 0;
         if ((e = dev_alloc(&w->rec, (size_t)n)) != cudaSuccess) return cuda_fail(e, "workspace");
         if ((e = dev_alloc(&w->rect, (size_t)n)) != cudaSuccess) return cuda_fail(e, "workspace");
+        if ((e = dev_alloc(&w->wt16, (size_t)n)) != cudaSuccess) return cuda_fail(e, "workspace");
         w->n_cap = n;
     }
     if (tiles + 1 > w->tiles_cap) {
@@ -249,6 +252,7 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     a.flags = opts->flags;
     a.rec = w->rec;
     a.rect = w->rect;
+    a.wt16 = w->wt16;
     a.tile_count = w->tile_count;
     a.tile_offsets = w->tile_offsets;
     a.tile_order = w->tile_order;
@@ -557,6 +561,7 @@ mgs_status mgs_workspace_destroy(mgs_workspace w) {
     DeviceGuard g(w->ctx->device);
     dev_free(w->rec);
     dev_free(w->rect);
+    dev_free(w->wt16);
     dev_free(w->tile_count);
     dev_free(w->tile_offsets);
     dev_free(w->tile_order);

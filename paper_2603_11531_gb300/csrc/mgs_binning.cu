@@ -106,14 +106,42 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const uint2 *__restri
     }
 }
 
+// Tensor-core weights of Gaussian g: (w c_r, w c_g, w c_b, w) times the
+// frame's power-of-two scale (2^(14 - e) when the largest weight has
+// exponent e >= 14), as FP16 high parts then FP16 low parts.
+__device__ __forceinline__ uint4 weights_f16(const ProjRec &r, float scale) {
+    const float w[4] = {-r.b.w * scale, -r.c.x * scale, -r.c.y * scale, -r.b.z * scale};
+    __half hi[4], lo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        hi[k] = __float2half_rn(w[k]);
+        lo[k] = __float2half_rn(w[k] - __half2float(hi[k]));
+    }
+    uint4 u;
+    u.x = (uint32_t)__half_as_ushort(hi[0]) | ((uint32_t)__half_as_ushort(hi[1]) << 16);
+    u.y = (uint32_t)__half_as_ushort(hi[2]) | ((uint32_t)__half_as_ushort(hi[3]) << 16);
+    u.z = (uint32_t)__half_as_ushort(lo[0]) | ((uint32_t)__half_as_ushort(lo[1]) << 16);
+    u.w = (uint32_t)__half_as_ushort(lo[2]) | ((uint32_t)__half_as_ushort(lo[3]) << 16);
+    return u;
+}
+
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(
     const uint2 *__restrict__ rect, int64_t n, int tiles_x, int T,
     const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ bases,
-    uint32_t *__restrict__ gids, uint64_t capacity, const DevStatus *__restrict__ status) {
+    uint32_t *__restrict__ gids, uint64_t capacity, const DevStatus *__restrict__ status,
+    const ProjRec *__restrict__ rec, uint4 *__restrict__ wt16) {
     extern __shared__ uint32_t cur_s[];
     if (status->last_pairs > capacity) return;  // overflow: lists are not built
     int64_t begin, end;
     cta_range(n, begin, end);
+    if (wt16) {   // tensor-core rasteriser: FP16 weights of the visible Gaussians
+        const int we = (int)((status->wmax_frame_bits >> 23) & 0xFFu) - 127;
+        const float scale = we >= 14 ? __int_as_float((127 + 14 - we) << 23) : 1.0f;
+        for (int64_t g = begin + threadIdx.x; g < end; g += blockDim.x) {
+            const uint2 r = rect[g];
+            if (r.x | r.y) wt16[g] = weights_f16(rec[g], scale);
+        }
+    }
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int band0 = 0; band0 < T; band0 += kBand) {
         const int bn = min(kBand, T - band0);
@@ -257,7 +285,8 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases,
     k_tile_order<<<1, kScanThreads, 0, stream>>>(a.tile_count, T, a.tile_order, a.status);
     if ((e = cudaGetLastError()) != cudaSuccess || a.n == 0) return e;
     k_bin_scatter<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, a.tile_offsets,
-                                                    bases, a.gids, a.capacity, a.status);
+                                                    bases, a.gids, a.capacity, a.status, a.rec,
+                                                    tc_raster(a) ? a.wt16 : nullptr);
     return cudaGetLastError();
 }
 

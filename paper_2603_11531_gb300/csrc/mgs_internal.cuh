@@ -120,6 +120,7 @@ struct RenderArgs {
     uint32_t *tile_offsets;   // [T + 1]
     uint32_t *tile_order;     // [T] rasterisation order (longest lists first)
     uint32_t *gids;           // [capacity]
+    uint4 *wt16;              // [n] tensor-core weights (FP16 high / low parts), see tc_raster()
     uint64_t capacity;
     DevStatus *status;
     // outputs
@@ -128,6 +129,14 @@ struct RenderArgs {
     int32_t *out_count;
     float *out_depth;          // depth image (Eq. 5), optional
 };
+
+// Does this render rasterise with tensor-core sums (FP16 attributes, no
+// comparator, no depth image, not forced onto the FMA pipe)?  Binning then
+// also converts every visible Gaussian's weights to FP16 (args.wt16).
+__host__ __device__ inline bool tc_raster(const RenderArgs &a) {
+    return a.precision == MGS_PREC_FP16 && a.out_depth == nullptr &&
+           (a.flags & (MGS_FLAG_RASTER_FMA | MGS_FLAG_SORTED)) == 0;
+}
 
 // Can Gaussian (m, l) include any pixel centre of the block centred at (bx, by)
 // with half extents (hx, hy)?  Sound for the exact FP32 test: the slab bounds

@@ -228,9 +228,10 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
 // FP32x2 operation serves both, and the packed pair of alphas is exactly the
 // A fragment the lane holds.  B = the chunk's weights [w c_r, w c_g, w c_b, w]
 // as FP16 high parts (columns 0-3) and low parts (columns 4-7), so column c +
-// column c + 4 is the sum with a 22-bit weight.  Weights are scaled by a
-// power of two when the frame's largest weight would overflow FP16 (the
-// scale cancels in A / B and is divided out).  T stays in FP32 FMAs.
+// column c + 4 is the sum with a 22-bit weight; binning prepares these FP16
+// weights once per Gaussian (k_bin_scatter), scaled by a power of two when
+// the frame's largest weight would overflow FP16 (the scale cancels in A / B
+// and is divided out here).  T stays in FP32 FMAs.
 constexpr int kTcThreads = 128;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kChunk = 8;        // candidates per MMA (K)
@@ -243,7 +244,7 @@ constexpr int kRing = 40;        // candidate slots per warp: five chunks
 //   geo[2][s / 2] = {l22(a), l22(b), log2 o(a), log2 o(b)}   (a = even slot)
 struct TcSmem {
     float4 geo[kTcWarps][3][kRing / 2];
-    __half wt[kTcWarps][8][kRing];        // weight column c of slot s (FP16)
+    uint4 wt[kTcWarps][kRing];            // slot s: its 8 FP16 weight columns
 };
 
 __device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
@@ -263,7 +264,7 @@ __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, 
 // lane's entries 2t, 2t + 1 at its eight pixels (same FP32 sequence as
 // accumulate()), T updated, alphas packed to FP16 and summed by four MMAs.
 template <bool kCount, bool kClamp>
-__device__ __forceinline__ void tc_chunk(const float4 (*geo)[kRing / 2], const __half (*wt)[kRing],
+__device__ __forceinline__ void tc_chunk(const float4 (*geo)[kRing / 2], const uint4 *wt,
                                          int c0, int g, int t, const f2 (&pxc)[8], f2 pyc,
                                          f2 kq2, float (&T)[8], float (&D)[4][4], int (&cnt)[8]) {
     const int pr = (c0 >> 1) + t;
@@ -297,7 +298,8 @@ __device__ __forceinline__ void tc_chunk(const float4 (*geo)[kRing / 2], const _
         T[j] = fmaf(-ab, T[j], T[j]);
         a[j] = h2bits(aa, ab);            // k = 2t (low half), 2t + 1
     }
-    const uint32_t b0 = reinterpret_cast<const uint32_t *>(wt[g])[(c0 >> 1) + t];
+    const unsigned short *wa = reinterpret_cast<const unsigned short *>(wt + c0 + 2 * t);
+    const uint32_t b0 = (uint32_t)wa[g] | ((uint32_t)wa[8 + g] << 16);   // column g, k = 2t, 2t + 1
 #pragma unroll
     for (int i = 0; i < 4; ++i) mma_k8(D[i], a[2 * i], a[2 * i + 1], b0);   // pixels 2i, 2i + 1
 }
@@ -312,7 +314,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     const int xb = bx0 + 8 * (g >> 2);
     const int py = by0 + (g & 3);
     float4(*geo)[kRing / 2] = sm.geo[warp];
-    __half(*wt)[kRing] = sm.wt[warp];
+    uint4 *wt = sm.wt[warp];
 
     const uint32_t start = args.tile_offsets[tile];
     const uint32_t end = args.tile_offsets[tile + 1];
@@ -342,34 +344,34 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
 
     int head = 0, count = 0;          // unprocessed candidates: ring slots [head, head + count)
     uint64_t clamp_mask = 0;          // ring slots whose opacity exceeds 0.99
-    // prefetch of the next batch: the fields the block test needs
+    // prefetch of the next batch: everything the block test and staging need
     float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f);
-    float l22_n = 0.f;
-    uint32_t gid_n = 0;
+    float2 b_n = make_float2(0.f, 0.f);
+    uint4 w_n = make_uint4(0u, 0u, 0u, 0u);
     if (start + lane < end) {
-        gid_n = __ldg(&args.gids[start + lane]);
-        a_n = __ldg(&args.rec[gid_n].a);
-        l22_n = __ldg(&args.rec[gid_n].b.x);
+        const uint32_t gid = __ldg(&args.gids[start + lane]);
+        a_n = __ldg(&args.rec[gid].a);
+        b_n = __ldg(reinterpret_cast<const float2 *>(&args.rec[gid].b));
+        w_n = __ldg(&args.wt16[gid]);
     }
     for (uint32_t base = start; base < end; base += 32) {
         const uint32_t j = base + lane;
         const float4 a = a_n;
-        const float l22 = l22_n;
-        const uint32_t gid = gid_n;
+        const float2 b = b_n;
+        const uint4 wv = w_n;
         const bool cand =
-            j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, l22, bcx, bcy, 7.5f, 1.5f));
+            j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bcx, bcy, 7.5f, 1.5f));
         if (j + 32 < end) {
-            gid_n = __ldg(&args.gids[j + 32]);
-            a_n = __ldg(&args.rec[gid_n].a);
-            l22_n = __ldg(&args.rec[gid_n].b.x);
+            const uint32_t gid = __ldg(&args.gids[j + 32]);
+            a_n = __ldg(&args.rec[gid].a);
+            b_n = __ldg(reinterpret_cast<const float2 *>(&args.rec[gid].b));
+            w_n = __ldg(&args.wt16[gid]);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         bool clamp = false;
         int pos = 0;
         if (cand) {
             pos = (head + count + __popc(bal & ((1u << lane) - 1u))) % kRing;
-            const float4 b = __ldg(&args.rec[gid].b);
-            const float2 c = __ldg(reinterpret_cast<const float2 *>(&args.rec[gid].c));
             float *q = reinterpret_cast<float *>(&geo[0][pos >> 1]);
             const int o = pos & 1;
             q[o] = a.x;
@@ -381,13 +383,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             q[o] = b.x;
             q[2 + o] = b.y;
             clamp = b.y > kLogClamp;
-            const float w4[4] = {-b.w * wscale, -c.x * wscale, -c.y * wscale, -b.z * wscale};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const __half hi = __float2half_rn(w4[k]);
-                wt[k][pos] = hi;
-                wt[k + 4][pos] = __float2half_rn(w4[k] - __half2float(hi));
-            }
+            wt[pos] = wv;                        // FP16 weights prepared during binning
         }
         // slots of this batch that need the 0.99 clamp
         const unsigned cb = __ballot_sync(0xffffffffu, clamp);
@@ -425,8 +421,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             q = reinterpret_cast<float *>(&geo[2][pos >> 1]);
             q[o] = 1.0f;
             q[2 + o] = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) wt[k][pos] = __float2half_rn(0.0f);
+            wt[pos] = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncwarp();
         if ((clamp_mask >> head) & 0xFFull)
@@ -493,9 +488,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
 
 // Tensor-core accumulation is used for FP16-attribute scenes unless the
 // caller asks for the FP32 FMA sums.
-__host__ __device__ __forceinline__ bool use_tc(const RenderArgs &a) {
-    return a.precision == MGS_PREC_FP16 && (a.flags & MGS_FLAG_RASTER_FMA) == 0;
-}
+__host__ __device__ __forceinline__ bool use_tc(const RenderArgs &a) { return tc_raster(a); }
 
 // One CTA per tile, longest tile lists first.
 template <bool kAux, bool kCount, bool kDepth = false>

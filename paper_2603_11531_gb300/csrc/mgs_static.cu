@@ -36,8 +36,9 @@ constexpr size_t kOffsetsOff = kCountOff + align256((kMaxTiles + 1) * sizeof(uin
 constexpr size_t kOrderOff = kOffsetsOff + align256((kMaxTiles + 1) * sizeof(uint32_t));
 constexpr size_t kBasesOff = kOrderOff + align256((kMaxTiles + 1) * sizeof(uint32_t));
 constexpr size_t kGidsOff = kBasesOff + align256((size_t)kMaxBinCtas * kMaxTiles * sizeof(uint32_t));
-constexpr size_t kStatusOff = kGidsOff + align256(kMaxPairs * sizeof(uint32_t));
-constexpr size_t kScratchBytes = kStatusOff + align256(sizeof(DevStatus));  // ~27 MiB
+constexpr size_t kWt16Off = kGidsOff + align256(kMaxPairs * sizeof(uint32_t));
+constexpr size_t kStatusOff = kWt16Off + align256(kMaxGaussians * sizeof(uint4));
+constexpr size_t kScratchBytes = kStatusOff + align256(sizeof(DevStatus));  // ~29 MiB
 
 // The scratch.  In host code this name is only a host-side stand-in for the
 // device array: its device address comes from cudaGetSymbolAddress.
@@ -130,6 +131,7 @@ extern "C" mgs_status mgs_render_static(const void *attrs, int64_t n, int32_t pr
     a.tile_offsets = reinterpret_cast<uint32_t *>(S + kOffsetsOff);
     a.tile_order = reinterpret_cast<uint32_t *>(S + kOrderOff);
     a.gids = reinterpret_cast<uint32_t *>(S + kGidsOff);
+    a.wt16 = reinterpret_cast<uint4 *>(S + kWt16Off);
     a.capacity = (uint64_t)kMaxPairs;
     a.status = reinterpret_cast<DevStatus *>(S + kStatusOff);
     a.out_rgb = out_rgb;
