@@ -83,6 +83,8 @@ def lib():
             L.orc_bin.restype = ctypes.c_int64
             L.orc_bin.argtypes = [ctypes.c_int64, P, ctypes.c_int, ctypes.c_int, P,
                                   P, ctypes.c_int64]
+            L.orc_tile_may_hit.restype = ctypes.c_int
+            L.orc_tile_may_hit.argtypes = [P, ctypes.c_int, ctypes.c_int]
             L.orc_includes.restype = ctypes.c_int
             L.orc_includes.argtypes = [P, ctypes.c_int, ctypes.c_int]
             L.orc_rasterize.restype = ctypes.c_int
@@ -283,6 +285,11 @@ def mlp_eval(mlp, x) -> np.ndarray:
 def includes(g_row: np.ndarray, px: int, py: int) -> bool:
     one = np.ascontiguousarray(np.asarray(g_row).reshape(1))
     return bool(lib().orc_includes(_ptr(one), int(px), int(py)))
+
+
+def tile_may_hit(g_row: np.ndarray, tx: int, ty: int) -> bool:
+    one = np.ascontiguousarray(np.asarray(g_row).reshape(1))
+    return bool(lib().orc_tile_may_hit(_ptr(one), int(tx), int(ty)))
 
 
 def included_pairs(g: np.ndarray, offsets, gids, width: int, height: int):

@@ -377,6 +377,42 @@ int orc_preprocess(int64_t n, const double *attrs, const orc_camera *cam,
 /* Tile binning: per-tile Gaussian lists, no depth order                      */
 /* ------------------------------------------------------------------------- */
 
+/* FP32 contract, binning: can Gaussian g include any pixel centre of tile
+ * (tx, ty)?  Slab bounds at the tile centre (bx, by) with half extent 7.5:
+ * every pixel p of the tile has |e1(p)| >= |e1c| - h1 and |e2(p)| >=
+ * |e2c| - h2 (exact arithmetic), and an included pixel has |e1|, |e2| <= 3;
+ * the margins m1, m2 (2^-18 relative) cover the rounding of both sides, so a
+ * tile that fails holds no included pixel.  One correctly rounded binary32
+ * operation per line, as the GPU evaluates it. */
+int orc_tile_may_hit(const orc_gauss *g, int tx, int ty)
+{
+    const float mx = g->m32[0], my = g->m32[1];
+    const float l11 = g->l32[0], l21 = g->l32[1], l22 = g->l32[2];
+    const float bx = (float)(tx * ORC_TILE + 8), by = (float)(ty * ORC_TILE + 8);
+    const float h = 7.5f;
+    const float dxb = bx - mx;
+    const float dyb = by - my;
+    const float t21 = l21 * dyb;
+    const float e1c = fabsf(fmaf(l11, dxb, t21));
+    const float a21 = fabsf(l21) * h;
+    const float h1 = fmaf(fabsf(l11), h, a21);
+    const float u1 = fabsf(dxb) + h;
+    const float u2 = fabsf(dyb) + h;
+    const float s11 = fabsf(l11) * u1;
+    const float s12 = fabsf(l21) * u2;
+    const float s1 = s11 + s12;
+    const float s1b = s1 + 4.0f;
+    const float m1 = 3.814697265625e-06f * s1b;
+    const float e2c = fabsf(l22 * dyb);
+    const float h2 = fabsf(l22) * h;
+    const float s2 = fabsf(l22) * u2;
+    const float s2b = s2 + 4.0f;
+    const float m2 = 3.814697265625e-06f * s2b;
+    const float d1 = e1c - h1, d2 = e2c - h2;
+    const float c1 = 3.0f + m1, c2 = 3.0f + m2;
+    return d1 <= c1 && d2 <= c2;
+}
+
 int64_t orc_bin(int64_t n, const orc_gauss *g, int tiles_x, int tiles_y,
                 int64_t *offsets, int32_t *gids, int64_t cap)
 {
@@ -386,7 +422,7 @@ int64_t orc_bin(int64_t n, const orc_gauss *g, int tiles_x, int tiles_y,
         if (!g[i].visible) continue;
         for (int ty = g[i].rect[1]; ty < g[i].rect[3]; ++ty)
             for (int tx = g[i].rect[0]; tx < g[i].rect[2]; ++tx)
-                offsets[(int64_t)ty * tiles_x + tx + 1] += 1;
+                if (orc_tile_may_hit(g + i, tx, ty)) offsets[(int64_t)ty * tiles_x + tx + 1] += 1;
     }
     for (int64_t t = 0; t < T; ++t) offsets[t + 1] += offsets[t];
     const int64_t K = offsets[T];
@@ -399,7 +435,7 @@ int64_t orc_bin(int64_t n, const orc_gauss *g, int tiles_x, int tiles_y,
         if (!g[i].visible) continue;
         for (int ty = g[i].rect[1]; ty < g[i].rect[3]; ++ty)
             for (int tx = g[i].rect[0]; tx < g[i].rect[2]; ++tx)
-                gids[cur[(int64_t)ty * tiles_x + tx]++] = (int32_t)i;
+                if (orc_tile_may_hit(g + i, tx, ty)) gids[cur[(int64_t)ty * tiles_x + tx]++] = (int32_t)i;
     }
     free(cur);
     return K;

@@ -125,6 +125,12 @@ int orc_preprocess(int64_t n, const double *attrs, const orc_camera *cam,
 int64_t orc_bin(int64_t n, const orc_gauss *g, int tiles_x, int tiles_y,
                 int64_t *offsets, int32_t *gids, int64_t cap);
 
+/* FP32-contract tile test of binning: 1 if Gaussian g may include a pixel
+ * centre of tile (tx, ty) (conservative slab bounds at the tile centre), 0 if
+ * it certainly includes none.  The tile lists hold the visible Gaussians whose
+ * rectangle contains the tile and that pass this test. */
+int orc_tile_may_hit(const orc_gauss *g, int tx, int ty);
+
 /* FP32-contract inclusion test of pixel (px, py) for Gaussian g. */
 int orc_includes(const orc_gauss *g, int px, int py);
 

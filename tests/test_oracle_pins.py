@@ -276,13 +276,19 @@ def test_bruteforce_tiles_and_pixels(oracle_lib, W, H, n, seed):
     out = oracle.render(attrs, cam, bg=bg, want_aux=True, want_count=True)
     g = out["gauss"]
     tx, ty = oracle.tiles(W, H)
-    # tile lists: every visible Gaussian whose rectangle overlaps the tile
+    # tile lists: the visible Gaussians whose rectangle overlaps the tile,
+    # minus those the tile test rules out -- and a Gaussian ruled out
+    # includes no pixel of the tile (brute force over the tile's pixels)
     for t in range(tx * ty):
         i, j = t % tx, t // tx
-        exp = [k for k in range(n) if g[k]["visible"] and g[k]["rect"][0] <= i < g[k]["rect"][2]
-               and g[k]["rect"][1] <= j < g[k]["rect"][3]]
+        in_rect = [k for k in range(n) if g[k]["visible"] and g[k]["rect"][0] <= i < g[k]["rect"][2]
+                   and g[k]["rect"][1] <= j < g[k]["rect"][3]]
         got = list(out["gids"][out["offsets"][t]:out["offsets"][t + 1]])
-        assert got == exp
+        assert got == [k for k in in_rect if k in got]
+        for k in set(in_rect) - set(got):
+            assert not any(oracle.includes(g[k], px, py)
+                           for py in range(16 * j, min(16 * j + 16, H))
+                           for px in range(16 * i, min(16 * i + 16, W)))
     # pixels: loop over ALL Gaussians with the same membership rule
     for py in range(H):
         for px in range(W):
