@@ -14,7 +14,10 @@
 //
 // Pairs are expanded warp-cooperatively: a warp's 32 Gaussians are flattened
 // into one pair index space (prefix sum of rectangle areas) so a Gaussian
-// covering thousands of tiles does not serialise one lane.  Order within a
+// covering thousands of tiles does not serialise one lane.  A pair is listed
+// only if the FP32 tile test (tile_may_hit) allows an included pixel in the
+// tile; its rectangle alone (the 3-sigma bounding square) would list many
+// tiles a thin ellipse never reaches.  Order within a
 // tile follows the atomics and is not reproducible; the rasteriser does not
 // depend on it beyond FP32 rounding.
 #include "mgs_internal.cuh"
@@ -33,15 +36,47 @@ __device__ __forceinline__ void rect_of(const uint2 r, int &x0, int &y0, int &w,
     h = (int)(r.y >> 16) - y0;
 }
 
+// FP32-contract tile test: may Gaussian (m, l) include a pixel centre of tile
+// (tx, ty)?  Slab bounds at the tile centre with half extent 7.5 and a 2^-18
+// relative margin, one correctly rounded operation per step (the oracle
+// evaluates the identical sequence, so both build the same lists).  A tile
+// that fails holds no pixel with q <= 9.
+__device__ __forceinline__ bool tile_may_hit(float mx, float my, float l11, float l21, float l22,
+                                             int tx, int ty) {
+    const float h = 7.5f;
+    const float bx = (float)(tx * kTile + 8), by = (float)(ty * kTile + 8);
+    const float dxb = __fsub_rn(bx, mx);
+    const float dyb = __fsub_rn(by, my);
+    const float e1c = fabsf(__fmaf_rn(l11, dxb, __fmul_rn(l21, dyb)));
+    const float h1 = __fmaf_rn(fabsf(l11), h, __fmul_rn(fabsf(l21), h));
+    const float u2 = __fadd_rn(fabsf(dyb), h);
+    const float s1 = __fadd_rn(__fmul_rn(fabsf(l11), __fadd_rn(fabsf(dxb), h)), __fmul_rn(fabsf(l21), u2));
+    const float m1 = __fmul_rn(3.814697265625e-06f, __fadd_rn(s1, 4.0f));
+    const float e2c = fabsf(__fmul_rn(l22, dyb));
+    const float h2 = __fmul_rn(fabsf(l22), h);
+    const float m2 = __fmul_rn(3.814697265625e-06f, __fadd_rn(__fmul_rn(fabsf(l22), u2), 4.0f));
+    return __fsub_rn(e1c, h1) <= __fadd_rn(3.0f, m1) && __fsub_rn(e2c, h2) <= __fadd_rn(3.0f, m2);
+}
+
 // Calls f(tile, gid) for every (tile, Gaussian) pair of Gaussians
-// [g0, g0 + 32) (one per lane), spreading the pairs over the warp's lanes.
+// [g0, g0 + 32) (one per lane) whose tile passes tile_may_hit, spreading the
+// pairs of the rectangles over the warp's lanes.
 template <class F>
-__device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect, int64_t n, int64_t g0,
+__device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
+                                           const ProjRec *__restrict__ rec, int64_t n, int64_t g0,
                                            int tiles_x, F &&f) {
     const int lane = threadIdx.x & 31;
     const int64_t i = g0 + lane;
     int x0 = 0, y0 = 0, w = 0, h = 0;
-    if (i < n) rect_of(rect[i], x0, y0, w, h);
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
+    float gl22 = 0.f;
+    if (i < n) {
+        rect_of(rect[i], x0, y0, w, h);
+        if (w > 0 && h > 0) {
+            ga = rec[i].a;
+            gl22 = rec[i].b.x;
+        }
+    }
     const int c = w * h;
     int incl = c;
 #pragma unroll
@@ -64,11 +99,16 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect, int64
         const int oy0 = __shfl_sync(0xffffffffu, y0, lo);
         const int ow = __shfl_sync(0xffffffffu, w, lo);
         const int oe = __shfl_sync(0xffffffffu, excl, lo);
+        const float mx = __shfl_sync(0xffffffffu, ga.x, lo);
+        const float my = __shfl_sync(0xffffffffu, ga.y, lo);
+        const float l11 = __shfl_sync(0xffffffffu, ga.z, lo);
+        const float l21 = __shfl_sync(0xffffffffu, ga.w, lo);
+        const float l22 = __shfl_sync(0xffffffffu, gl22, lo);
         if (p < P) {
             const int k = p - oe;
             const int ky = k / ow;
-            const int tile = (oy0 + ky) * tiles_x + ox0 + (k - ky * ow);
-            f(tile, (uint32_t)(g0 + lo));
+            const int tx = ox0 + (k - ky * ow), ty = oy0 + ky;
+            if (tile_may_hit(mx, my, l11, l21, l22, tx, ty)) f(ty * tiles_x + tx, (uint32_t)(g0 + lo));
         }
     }
 }
@@ -80,6 +120,7 @@ __device__ __forceinline__ void cta_range(int64_t n, int64_t &begin, int64_t &en
 }
 
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(const uint2 *__restrict__ rect,
+                                                           const ProjRec *__restrict__ rec,
                                                            int64_t n, int tiles_x, int T,
                                                            uint32_t *__restrict__ tile_count,
                                                            uint32_t *__restrict__ bases) {
@@ -92,7 +133,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const uint2 *__restri
         for (int t = threadIdx.x; t < bn; t += blockDim.x) cnt_s[t] = 0u;
         __syncthreads();
         for (int64_t g0 = begin + 32 * warp; g0 < end; g0 += 32 * nwarps) {
-            warp_pairs(rect, end, g0, tiles_x, [&](int tile, uint32_t) {
+            warp_pairs(rect, rec, end, g0, tiles_x, [&](int tile, uint32_t) {
                 const int t = tile - band0;
                 if ((unsigned)t < (unsigned)bn) atomicAdd(&cnt_s[t], 1u);
             });
@@ -150,7 +191,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(
             cur_s[t] = offsets[band0 + t] + bases[(int64_t)blockIdx.x * T + band0 + t];
         __syncthreads();
         for (int64_t g0 = begin + 32 * warp; g0 < end; g0 += 32 * nwarps) {
-            warp_pairs(rect, end, g0, tiles_x, [&](int tile, uint32_t gid) {
+            warp_pairs(rect, rec, end, g0, tiles_x, [&](int tile, uint32_t gid) {
                 const int t = tile - band0;
                 if ((unsigned)t < (unsigned)bn) {
                     const uint32_t slot = atomicAdd(&cur_s[t], 1u);
@@ -276,8 +317,8 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases,
         if ((e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(kBand * sizeof(uint32_t)))) != cudaSuccess)
             return e;
-        k_bin_count<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, a.tile_count,
-                                                      bases);
+        k_bin_count<<<C, kBinThreads, smem, stream>>>(a.rect, a.rec, a.n, a.cam.tiles_x, T,
+                                                      a.tile_count, bases);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_scan<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, T, a.capacity, a.status);
