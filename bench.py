@@ -324,6 +324,8 @@ def run_gpu(args):
             line["large"] = run_large(m, torch, local)
         if world == 1 and not args.no_paper_mlp:
             line["paper_width_mlp"] = run_paper_mlp(m, torch, local)
+        if world == 1 and not args.no_backward:
+            line["backward"] = run_backward(m, torch, local)
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline_sample()
             cb.pop("seconds", None)
@@ -499,6 +501,55 @@ def run_paper_mlp(m, torch, local, reps=2):
             "mlp_tflops_in_preprocess": flops / (per[0] / 1000.0) / 1e12}
 
 
+def run_backward(m, torch, local, steps=10):
+    """One training step of the renderer on the 300k workload (unbounded
+    distribution, FP32 attributes, MLP on, 1296x840): forward with the saved
+    (A, B, T) planes, the L1 loss gradient sign(C - C*) / (3 H W) on the
+    device, and the adjoint (mgs_render_backward) for every stored parameter
+    and the MLP weights.  CUDA events around each stage."""
+    from paper_2603_11531_gb300 import synth
+    scene, cam, target = synth.workload_backward_300k()
+    r = m.Renderer(local)
+    h = r.load_scene(scene)
+    H, W = cam.height, cam.width
+    opts = m.render_opts(use_mlp=True)
+    stream = torch.cuda.Stream(device=local)
+    rgb = torch.empty((H, W, 3), device="cuda")
+    aux = torch.empty((5, H, W), device="cuda")
+    tgt = torch.from_numpy(target).cuda()
+    d_attrs = torch.empty((scene.n, 24), device="cuda")
+    d_mlp = torch.empty(m.MLP_GRAD_SIZE, device="cuda")
+    m.mgs_render_checked(r.ws, h, cam, opts, rgb, aux, None, stream)
+
+    def step(ev):
+        ev[0].record(stream)
+        m.mgs_render(r.ws, h, cam, opts, rgb, aux, None, stream)
+        ev[1].record(stream)
+        with torch.cuda.stream(stream):
+            dL = torch.sign(rgb - tgt) / float(rgb.numel())
+        ev[2].record(stream)
+        m.mgs_render_backward(r.ws, h, cam, opts, dL, aux, d_attrs, d_mlp, stream)
+        ev[3].record(stream)
+
+    for _ in range(3):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    fwd, bwd, tot = [], [], []
+    for _ in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        step(ev)
+        ev[3].synchronize()
+        fwd.append(ev[0].elapsed_time(ev[1]))
+        bwd.append(ev[2].elapsed_time(ev[3]))
+        tot.append(ev[0].elapsed_time(ev[3]))
+    st, _ = m.mgs_workspace_sync(r.ws, stream, allow_overflow=True)
+    if st != m.MGS_OK:
+        raise RuntimeError("backward workload overflowed its tile lists")
+    r.close()
+    return {"gaussians": scene.n, "resolution": [W, H], "attrs": "fp32", "mlp": "bf16 22-64-64-5",
+            "forward_ms": statistics.median(fwd), "backward_ms": statistics.median(bwd),
+            "step_ms": statistics.median(tot), "steps_per_s": 1000.0 / statistics.median(tot)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -509,6 +560,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-paper-mlp", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -78,6 +78,7 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
         }
     }
     const int c = w * h;
+    const float winv = w > 0 ? 1.0f / (float)w : 0.0f;
     int incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -98,6 +99,7 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
         const int ox0 = __shfl_sync(0xffffffffu, x0, lo);
         const int oy0 = __shfl_sync(0xffffffffu, y0, lo);
         const int ow = __shfl_sync(0xffffffffu, w, lo);
+        const float oinv = __shfl_sync(0xffffffffu, winv, lo);
         const int oe = __shfl_sync(0xffffffffu, excl, lo);
         const float mx = __shfl_sync(0xffffffffu, ga.x, lo);
         const float my = __shfl_sync(0xffffffffu, ga.y, lo);
@@ -106,7 +108,11 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
         const float l22 = __shfl_sync(0xffffffffu, gl22, lo);
         if (p < P) {
             const int k = p - oe;
-            const int ky = k / ow;
+            // k / ow via the reciprocal, then corrected by one step either way
+            // (the product is off by at most 2^-23 (k + 0.5) / ow < 1 for any k < 2^23)
+            int ky = (int)(((float)k + 0.5f) * oinv);
+            if (ky * ow > k) --ky;
+            else if ((ky + 1) * ow <= k) ++ky;
             const int tx = ox0 + (k - ky * ow), ty = oy0 + ky;
             if (tile_may_hit(mx, my, l11, l21, l22, tx, ty)) f(ty * tiles_x + tx, (uint32_t)(g0 + lo));
         }
