@@ -24,6 +24,7 @@ namespace mgs {
 namespace {
 
 constexpr int kBwdThreads = 64;   // raster backward: two warps per tile
+constexpr int kRedGroup = 8;      // candidates reduced together through shared memory
 constexpr int kGRec = 12;         // per-Gaussian raster gradient record
 // layout: dc(3), dw, do, dm(2), dK(3) [conic A, B, C], pad(2)
 
@@ -44,6 +45,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
                                                             const float *__restrict__ aux,
                                                             float *__restrict__ gG) {
     __shared__ float4 buf[2][4][32];
+    // per warp: the partials of up to kRedGroup candidates, row (k, e), column
+    // lane; rows padded to 36 floats so eight lanes reading eight rows with
+    // 16-byte loads hit distinct banks
+    __shared__ __align__(16) float red[2][kRedGroup * 10][36];
     const DevCamera &cam = args.cam;
     const int tile = (int)args.tile_order[blockIdx.x];
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
@@ -109,17 +114,20 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
             const float w = -b.z, o = exp2f(b.y);
             const float iw = 1.0f / w;
             wb[0][pos] = a;
-            wb[1][pos] = make_float4(b.x, b.y, o, w);
+            // 1/o (0 when o = 0: no opacity gradient then)
+            wb[1][pos] = make_float4(b.x, b.y, o > 0.0f ? 1.0f / o : 0.0f, w);
             // colour c = (-w c) / (-w); conic (A, B, C) = L L^T from the factors
             wb[2][pos] = make_float4(-b.w * iw, -c.x * iw, -c.y * iw, a.z * a.z);
             wb[3][pos] = make_float4(a.z * a.w, a.w * a.w + b.x * b.x, __uint_as_float(gid), 0.f);
         }
         __syncwarp();
         const int nc = __popc(bal);
-        for (int k = 0; k < nc; ++k) {
+        for (int k0 = 0; k0 < nc; k0 += kRedGroup) {
+        const int ng = min(kRedGroup, nc - k0);
+        for (int k = k0; k < k0 + ng; ++k) {
             const float4 s0 = wb[0][k], s1 = wb[1][k], s2 = wb[2][k], s3 = wb[3][k];
             const float mx = s0.x, my = s0.y, l11 = s0.z, l21 = s0.w;
-            const float l22 = s1.x, lo = s1.y, o = s1.z, w = s1.w;
+            const float l22 = s1.x, lo = s1.y, io = s1.z, w = s1.w;
             const float cr = s2.x, cg = s2.y, cb = s2.z, cA = s2.w, cB = s3.x, cC = s3.y;
             float acc[10];
 #pragma unroll
@@ -137,14 +145,15 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
                 const float araw = ex2f(__fmaf_rn(q, kq, lo));
                 const float al = fminf(araw, 0.99f);
                 const float Gc = G[px][0] * cr + G[px][1] * cg + G[px][2] * cb;
-                const float gal = w * kA[px] * (Gc - Gr[px]) - Tp[px] / (1.0f - al) * Gbr[px];
+                // 1 - al >= 0.01: the fast reciprocal division is accurate to a few ulp
+                const float gal = w * kA[px] * (Gc - Gr[px]) - __fdividef(Tp[px], 1.0f - al) * Gbr[px];
                 const float kc = kA[px] * al * w;
                 acc[0] += kc * G[px][0];
                 acc[1] += kc * G[px][1];
                 acc[2] += kc * G[px][2];
                 acc[3] += kA[px] * al * (Gc - Gr[px]);
-                if (araw < 0.99f && o > 0.0f) {
-                    acc[4] += gal * (al / o);
+                if (araw < 0.99f && io > 0.0f) {
+                    acc[4] += gal * (al * io);
                     const float gq = -0.5f * al * gal;
                     acc[5] += -2.0f * gq * (cA * dx + cB * dy);
                     acc[6] += -2.0f * gq * (cB * dx + cC * dy);
@@ -154,12 +163,25 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
                 }
             }
 #pragma unroll
-            for (int e = 0; e < 10; ++e) acc[e] = warp_sum(acc[e]);
-            if (lane == 0) {
-                float *dst = gG + (size_t)__float_as_uint(s3.z) * kGRec;
+            for (int e = 0; e < 10; ++e) red[warp][(k - k0) * 10 + e][lane] = acc[e];
+        }
+        __syncwarp();
+        // transposed reduction: lane r sums row r (one candidate's partial e over
+        // the 32 lanes) and adds it to that candidate's gradient record
+        for (int r = lane; r < ng * 10; r += 32) {
+            const float4 *row = reinterpret_cast<const float4 *>(red[warp][r]);
+            float sum = 0.f;
 #pragma unroll
-                for (int e = 0; e < 10; ++e) atomicAdd(dst + e, acc[e]);
+            for (int v = 0; v < 8; ++v) {
+                const float4 x = row[v];
+                sum += (x.x + x.y) + (x.z + x.w);
             }
+            if (sum != 0.0f) {
+                const int k = k0 + r / 10;
+                atomicAdd(gG + (size_t)__float_as_uint(wb[3][k].z) * kGRec + (r % 10), sum);
+            }
+        }
+        __syncwarp();
         }
         __syncwarp();
     }
