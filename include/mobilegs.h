@@ -110,8 +110,15 @@ typedef struct {
     const uint16_t *mlp_w4; /* head of the paper-width MLP, else NULL */
     const float *mlp_b4;
     int32_t mlp_hidden[3];  /* {0, 0, 0} or three hidden widths */
-    int32_t reserved;       /* 0 */
+    int32_t order;          /* storage order, MGS_ORDER_* (0: automatic) */
 } mgs_scene_desc;
+
+/* Storage order of a loaded scene.  Spatial order (a Morton curve of the
+ * means) keeps the tile-list writes of binning local, which pays once the
+ * lists outgrow the L2 cache; for smaller scenes the given (random) order
+ * spreads binning's shared-memory atomics better.  Automatic: spatial above
+ * 2^21 Gaussians. */
+enum { MGS_ORDER_AUTO = 0, MGS_ORDER_SPATIAL = 1, MGS_ORDER_AS_GIVEN = 2 };
 
 /* Pinhole camera, world->camera (R row-major, t), OpenCV axes (x right,
  * y down, z forward).  Pixel (x, y) has its centre at (x + 0.5, y + 0.5). */
@@ -144,7 +151,10 @@ mgs_status mgs_ctx_info(mgs_ctx ctx, int32_t *sm_count, int64_t *free_bytes,
 
 /* Copy a scene into library-owned device memory (stream-ordered on
  * `stream`; the copy has completed when the call returns, so host buffers
- * may be reused at once).  MLP weights are repacked for the tensor cores. */
+ * may be reused at once).  MLP weights are repacked for the tensor cores.
+ * The library may store the Gaussians in its own order (desc->order);
+ * images do not depend on it, and every per-Gaussian output (tile lists,
+ * gradients) uses the caller's indices. */
 mgs_status mgs_load_scene(mgs_ctx ctx, const mgs_scene_desc *desc,
                           mgs_stream stream, mgs_scene *out);
 mgs_status mgs_unload_scene(mgs_scene scene);
@@ -244,9 +254,10 @@ mgs_status mgs_render_to_host(mgs_workspace ws, mgs_scene scene,
 /* Tile lists of the workspace's most recent render, for tests.  Waits for
  * `stream`, then reports n_tiles and n_pairs (= offsets[n_tiles]); if both
  * output buffers are non-NULL it also copies offsets [n_tiles + 1] and
- * gids [n_pairs] into them (caller-owned device memory).  Each tile's
- * Gaussian indices are in unspecified order.  MGS_ERR_OVERFLOW if that render
- * overflowed (its lists are incomplete). */
+ * gids [n_pairs] into them (caller-owned device memory).  Gaussian indices
+ * are the caller's (as in the scene description; the scene must still be
+ * loaded), in unspecified order within a tile.  MGS_ERR_OVERFLOW if that
+ * render overflowed (its lists are incomplete). */
 mgs_status mgs_tile_lists(mgs_workspace ws, mgs_stream stream, int64_t *n_tiles,
                           int64_t *n_pairs, uint32_t *offsets_out,
                           uint32_t *gids_out);

@@ -33,6 +33,9 @@ MGS_FLAG_NO_CULL = 1
 MGS_FLAG_SORTED = 2
 MGS_FLAG_MLP_MMA_SYNC = 4
 MGS_FLAG_RASTER_FMA = 8
+MGS_ORDER_AUTO = 0
+MGS_ORDER_SPATIAL = 1
+MGS_ORDER_AS_GIVEN = 2
 
 # Every entry point declared in include/mobilegs.h.
 EXPORTS = (
@@ -74,7 +77,7 @@ class mgs_scene_desc(ctypes.Structure):
                 ("mlp_w2", ctypes.c_void_p), ("mlp_b2", ctypes.c_void_p),
                 ("mlp_w3", ctypes.c_void_p), ("mlp_b3", ctypes.c_void_p),
                 ("mlp_w4", ctypes.c_void_p), ("mlp_b4", ctypes.c_void_p),
-                ("mlp_hidden", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32)]
+                ("mlp_hidden", ctypes.c_int32 * 3), ("order", ctypes.c_int32)]
 
 
 class mgs_sh_mlp(ctypes.Structure):
@@ -198,9 +201,11 @@ def mgs_ctx_info(ctx):
     return sm.value, fr.value, tot.value
 
 
-def mgs_load_scene(ctx, attrs, mlp=None, stream=None):
-    """attrs: (N, 24) float32/float16 numpy array or CUDA torch tensor."""
+def mgs_load_scene(ctx, attrs, mlp=None, stream=None, order=MGS_ORDER_AUTO):
+    """attrs: (N, 24) float32/float16 numpy array or CUDA torch tensor;
+    order: MGS_ORDER_* storage order (images and indices do not depend on it)."""
     d = mgs_scene_desc()
+    d.order = int(order)
     keep = []
     on_dev = hasattr(attrs, "is_cuda") and attrs.is_cuda
     if on_dev:
@@ -381,11 +386,11 @@ class Renderer:
         self.ws = mgs_workspace_create(self.ctx)
         self._scenes = []
 
-    def load_scene(self, scene_or_attrs, mlp=None, stream=None):
+    def load_scene(self, scene_or_attrs, mlp=None, stream=None, order=MGS_ORDER_AUTO):
         attrs = getattr(scene_or_attrs, "attrs", scene_or_attrs)
         if mlp is None:
             mlp = getattr(scene_or_attrs, "mlp", None)
-        h = mgs_load_scene(self.ctx, attrs, mlp, stream)
+        h = mgs_load_scene(self.ctx, attrs, mlp, stream, order)
         self._scenes.append(h)
         return h
 

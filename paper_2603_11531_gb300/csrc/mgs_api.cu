@@ -77,6 +77,8 @@ struct mgs_scene_s {
     bool has_mlp = false;
     unsigned char *mlp_blob = nullptr;  // packed weights + biases
     DevMLP mlp{};
+    uint32_t *perm = nullptr;    // stored row -> caller index (spatial order)
+    uint32_t *iperm = nullptr;   // caller index -> stored row
     int64_t bytes = 0;
 };
 
@@ -104,6 +106,7 @@ struct mgs_workspace_s {
     int64_t ss_n_cap = 0, ss_pairs_cap = 0;
     DevStatus *status = nullptr;
     int64_t last_tiles = 0;
+    const uint32_t *last_perm = nullptr;   // storage -> caller order of the last scene
     uint64_t grow_hint = 0;  // pairs needed by an overflowed render
     bool timing = false;
     std::vector<cudaEvent_t> event_pool;
@@ -253,6 +256,8 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     a.rec = w->rec;
     a.rect = w->rect;
     a.wt16 = w->wt16;
+    a.perm = s->perm;
+    a.iperm = s->iperm;
     a.tile_count = w->tile_count;
     a.tile_offsets = w->tile_offsets;
     a.tile_order = w->tile_order;
@@ -311,11 +316,13 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
             w->pending.push_back(ev);
         }
         w->last_tiles = T;
+        w->last_perm = s->perm;
         return MGS_OK;
     }
     if (prep) {
         *prep = a;
         w->last_tiles = T;
+        w->last_perm = s->perm;
         return MGS_OK;
     }
     if (bwd) {
@@ -349,6 +356,7 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
         w->pending.push_back(ev);
     }
     w->last_tiles = T;
+    w->last_perm = s->perm;
     return MGS_OK;
 }
 
@@ -420,6 +428,8 @@ mgs_status mgs_load_scene(mgs_ctx ctx, const mgs_scene_desc *d, mgs_stream strea
         return fail(MGS_ERR_INVALID_ARG, "n = %lld outside 0..2^31", (long long)d->n);
     if (d->precision != MGS_PREC_FP32 && d->precision != MGS_PREC_FP16)
         return fail(MGS_ERR_INVALID_ARG, "unknown precision %d", d->precision);
+    if (d->order < MGS_ORDER_AUTO || d->order > MGS_ORDER_AS_GIVEN)
+        return fail(MGS_ERR_INVALID_ARG, "unknown storage order %d", d->order);
     if (d->n > 0 && !d->attrs) return fail(MGS_ERR_INVALID_ARG, "attrs is NULL");
     const size_t elem = d->precision == MGS_PREC_FP16 ? 2 : 4;
     if (d->attrs_on_device && (reinterpret_cast<uintptr_t>(d->attrs) & 15))
@@ -446,17 +456,30 @@ mgs_status mgs_load_scene(mgs_ctx ctx, const mgs_scene_desc *d, mgs_stream strea
     s->n = d->n;
     s->precision = d->precision;
     const size_t bytes = (size_t)d->n * kRec * elem;
+    const bool spatial = d->n > 1 && (d->order == MGS_ORDER_SPATIAL ||
+                                      (d->order == MGS_ORDER_AUTO && d->n > (int64_t(1) << 21)));
     cudaError_t e = cudaMalloc(&s->attrs, bytes ? bytes : 16);
+    if (e == cudaSuccess && spatial) e = cudaMalloc(&s->perm, (size_t)d->n * 4);
+    if (e == cudaSuccess && spatial) e = cudaMalloc(&s->iperm, (size_t)d->n * 4);
     if (e != cudaSuccess) {
+        dev_free(s->perm);
+        dev_free(s->iperm);
+        if (s->attrs) cudaFree(s->attrs);
         delete s;
         return cuda_fail(e, "scene allocation");
     }
-    if (bytes) {
-        e = cudaMemcpyAsync(s->attrs, d->attrs, bytes,
-                            d->attrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            stream);
+    const cudaMemcpyKind kind = d->attrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (bytes && spatial) {
+        // upload, then store in spatial (Morton) order
+        void *tmp = nullptr;
+        e = cudaMalloc(&tmp, bytes);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, d->attrs, bytes, kind, stream);
+        if (e == cudaSuccess) e = spatial_order(tmp, d->n, d->precision, s->attrs, s->perm, s->iperm, stream);
+        if (tmp) cudaFree(tmp);
+    } else if (bytes) {
+        e = cudaMemcpyAsync(s->attrs, d->attrs, bytes, kind, stream);
     }
-    s->bytes = (int64_t)bytes;
+    s->bytes = (int64_t)bytes + (spatial ? (int64_t)d->n * 8 : 0);
     if (e == cudaSuccess && all_mlp && wide) {
         // pack: w1 [h1][32] (cols 22.. zero), w2 [h2][h1], w3 [h3][h2],
         // w4 [8][h3] (rows 5.. zero), then FP32 b1 [h1], b2 [h2], b3 [h3], b4 [8]
@@ -529,6 +552,8 @@ mgs_status mgs_load_scene(mgs_ctx ctx, const mgs_scene_desc *d, mgs_stream strea
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
         dev_free(s->mlp_blob);
+        dev_free(s->perm);
+        dev_free(s->iperm);
         cudaFree(s->attrs);
         delete s;
         return cuda_fail(e, "scene upload");
@@ -542,6 +567,8 @@ mgs_status mgs_unload_scene(mgs_scene s) {
     DeviceGuard g(s->ctx->device);
     cudaFree(s->attrs);
     dev_free(s->mlp_blob);
+    dev_free(s->perm);
+    dev_free(s->iperm);
     delete s;
     return MGS_OK;
 }
@@ -736,8 +763,13 @@ mgs_status mgs_tile_lists(mgs_workspace w, mgs_stream stream_, int64_t *n_tiles,
     if (offsets_out && gids_out) {
         e = cudaMemcpy(offsets_out, w->tile_offsets, (size_t)(w->last_tiles + 1) * 4,
                        cudaMemcpyDeviceToDevice);
-        if (e == cudaSuccess && h.last_pairs)
-            e = cudaMemcpy(gids_out, w->gids, (size_t)h.last_pairs * 4, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess && h.last_pairs) {
+            // list entries index the scene's stored (spatial) order: report caller indices
+            e = w->last_perm ? map_ids(w->gids, w->last_perm, (int64_t)h.last_pairs, gids_out, stream)
+                             : cudaMemcpy(gids_out, w->gids, (size_t)h.last_pairs * 4,
+                                          cudaMemcpyDeviceToDevice);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "tile list copy");
     }
     return MGS_OK;

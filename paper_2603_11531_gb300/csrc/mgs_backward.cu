@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_preprocess_bwd(RenderArgs args,
             (void)dphi;
         }
         if (!valid) continue;
-        float *out = d_attrs + (size_t)i * kRec;
+        float *out = d_attrs + (size_t)(args.perm ? args.perm[i] : (uint32_t)i) * kRec;
         if (!vis) {
 #pragma unroll
             for (int k = 0; k < kRec; ++k) out[k] = 0.f;

@@ -121,6 +121,8 @@ struct RenderArgs {
     uint32_t *tile_order;     // [T] rasterisation order (longest lists first)
     uint32_t *gids;           // [capacity]
     uint4 *wt16;              // [n] tensor-core weights (FP16 high / low parts), see tc_raster()
+    const uint32_t *perm;     // [n] stored position -> caller index (null: identity)
+    const uint32_t *iperm;    // [n] caller index -> stored position (null: identity)
     uint64_t capacity;
     DevStatus *status;
     // outputs
@@ -165,6 +167,18 @@ struct SortedScratch {
     uint32_t *hist;                // [sorted_hist_entries(max(n, capacity))]
 };
 int64_t sorted_hist_entries(int64_t n_max);
+// Stable LSD radix sort of (key, value) pairs by key bits [begin_bit, end_bit).
+cudaError_t radix_sort(uint64_t **k, uint32_t **v, uint64_t **kt, uint32_t **vt, int64_t n_max,
+                       const unsigned long long *n_dev, int begin_bit, int end_bit,
+                       uint32_t *hist, cudaStream_t stream);
+// Load-time spatial order (mgs_order.cu): attrs_out = attrs_in sorted along a
+// Morton curve of the means; perm[j] = caller index of stored row j, iperm
+// its inverse.  Synchronous.
+cudaError_t spatial_order(const void *attrs_in, int64_t n, int precision, void *attrs_out,
+                          uint32_t *perm, uint32_t *iperm, cudaStream_t stream);
+// out[j] = perm[in[j]] for j < count.
+cudaError_t map_ids(const uint32_t *in, const uint32_t *perm, int64_t count, uint32_t *out,
+                    cudaStream_t stream);
 // Depth-sorts every tile list and blends front to back (Eq. 11 comparator).
 cudaError_t launch_sorted(const RenderArgs &a, const SortedScratch &s, cudaStream_t stream);
 

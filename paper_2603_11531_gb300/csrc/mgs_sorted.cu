@@ -176,15 +176,19 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
 
 // Keys of the depth ranking: view depth bits (positive floats order as
 // unsigned integers) in the high word, invisible Gaussians last.
+// The input is laid out in caller order (j -> stored row iperm[j]), so the
+// stable sort breaks depth ties by caller index.
 __global__ void k_depth_keys(const ProjRec *__restrict__ rec, const uint2 *__restrict__ rect,
-                             int64_t n, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+                             const uint32_t *__restrict__ iperm, int64_t n,
+                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t i = iperm ? iperm[j] : (uint32_t)j;
     const uint2 r = rect[i];
     const bool vis = (r.x >> 16) > (r.x & 0xFFFF);
     const uint32_t d = vis ? __float_as_uint(rec[i].c.z) : 0xFFFFFFFFu;
-    keys[i] = (uint64_t)d << 32;
-    vals[i] = (uint32_t)i;
+    keys[j] = (uint64_t)d << 32;
+    vals[j] = i;
 }
 
 __global__ void k_rank_scatter(const uint32_t *__restrict__ sorted_idx, int64_t n,
@@ -315,6 +319,8 @@ int bits_for(uint64_t v) {
     return b;
 }
 
+}  // namespace
+
 // Sorts (key, value) pairs by bits [begin_bit, end_bit) of the key (stable
 // LSD, 4-bit digits).  n_max bounds the element count and sizes the grids;
 // n_dev (nullable) holds the actual count on the device.  The result is in
@@ -337,8 +343,6 @@ cudaError_t radix_sort(uint64_t **k, uint32_t **v, uint64_t **kt, uint32_t **vt,
     return cudaSuccess;
 }
 
-}  // namespace
-
 int64_t sorted_hist_entries(int64_t n_max) { return kRsBins * ((n_max + kRsTile - 1) / kRsTile); }
 
 cudaError_t launch_sorted(const RenderArgs &a, const SortedScratch &s, cudaStream_t stream) {
@@ -348,7 +352,8 @@ cudaError_t launch_sorted(const RenderArgs &a, const SortedScratch &s, cudaStrea
     if (a.n > 0) {
         uint64_t *k = s.nkeys, *kt = s.nkeys_tmp;
         uint32_t *v = s.nvals, *vt = s.nvals_tmp;
-        k_depth_keys<<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(a.rec, a.rect, a.n, k, v);
+        k_depth_keys<<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(a.rec, a.rect, a.iperm, a.n,
+                                                                         k, v);
         if ((e = radix_sort(&k, &v, &kt, &vt, a.n, nullptr, 32, 64, s.hist, stream)) != cudaSuccess)
             return e;
         k_rank_scatter<<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(v, a.n, s.rank);
