@@ -103,7 +103,7 @@ struct mgs_workspace_s {
     float *bwd_partials = nullptr; // backward: per-CTA MLP weight gradients
     int64_t bwd_partials_cap = 0;
     SortedScratch ss{};            // sorted comparator scratch
-    int64_t ss_n_cap = 0, ss_pairs_cap = 0;
+    int64_t ss_n_cap = 0, ss_pairs_cap = 0, ss_tiles_cap = 0;
     DevStatus *status = nullptr;
     int64_t last_tiles = 0;
     const uint32_t *last_perm = nullptr;   // storage -> caller order of the last scene
@@ -294,21 +294,25 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
         if (out_aux) return fail(MGS_ERR_INVALID_ARG, "the sorted comparator has no aux output");
         const int64_t nc = s->n > 0 ? s->n : 1;
         const int64_t pc = (int64_t)w->pair_cap;
-        if (nc > w->ss_n_cap || pc > w->ss_pairs_cap) {
+        if (nc > w->ss_n_cap || pc > w->ss_pairs_cap || T > w->ss_tiles_cap) {
             SortedScratch &q = w->ss;
             dev_free(q.nkeys); dev_free(q.nkeys_tmp); dev_free(q.nvals); dev_free(q.nvals_tmp);
             dev_free(q.rank); dev_free(q.keys); dev_free(q.keys_tmp); dev_free(q.vals);
-            dev_free(q.vals_tmp); dev_free(q.hist);
-            w->ss_n_cap = w->ss_pairs_cap = 0;
-            const int64_t hn = sorted_hist_entries(nc > pc ? nc : pc);
+            dev_free(q.vals_tmp);
+            if (q.temp) cudaFree(q.temp);
+            q.temp = nullptr;
+            w->ss_n_cap = w->ss_pairs_cap = w->ss_tiles_cap = 0;
+            q.temp_bytes = sorted_temp_bytes(nc, pc, (int)T);
             if ((e = dev_alloc(&q.nkeys, nc)) != cudaSuccess || (e = dev_alloc(&q.nkeys_tmp, nc)) != cudaSuccess ||
                 (e = dev_alloc(&q.nvals, nc)) != cudaSuccess || (e = dev_alloc(&q.nvals_tmp, nc)) != cudaSuccess ||
                 (e = dev_alloc(&q.rank, nc)) != cudaSuccess || (e = dev_alloc(&q.keys, pc)) != cudaSuccess ||
                 (e = dev_alloc(&q.keys_tmp, pc)) != cudaSuccess || (e = dev_alloc(&q.vals, pc)) != cudaSuccess ||
-                (e = dev_alloc(&q.vals_tmp, pc)) != cudaSuccess || (e = dev_alloc(&q.hist, hn)) != cudaSuccess)
+                (e = dev_alloc(&q.vals_tmp, pc)) != cudaSuccess ||
+                (e = cudaMalloc(&q.temp, q.temp_bytes ? q.temp_bytes : 16)) != cudaSuccess)
                 return cuda_fail(e, "sorted scratch");
             w->ss_n_cap = nc;
             w->ss_pairs_cap = pc;
+            w->ss_tiles_cap = T;
         }
         if ((e = launch_sorted(a, w->ss, stream)) != cudaSuccess) return cuda_fail(e, "sorted launch");
         if (w->timing) {
@@ -606,7 +610,7 @@ mgs_status mgs_workspace_destroy(mgs_workspace w) {
     dev_free(w->ss.keys_tmp);
     dev_free(w->ss.vals);
     dev_free(w->ss.vals_tmp);
-    dev_free(w->ss.hist);
+    if (w->ss.temp) cudaFree(w->ss.temp);
     dev_free(w->status);
     for (auto &q : w->pending)
         for (auto x : q) cudaEventDestroy(x);

@@ -34,12 +34,6 @@ __device__ __forceinline__ float ex2f(float x) {
     return y;
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
                                                             const float *__restrict__ dL,
                                                             const float *__restrict__ aux,

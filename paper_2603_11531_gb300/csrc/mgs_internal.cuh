@@ -159,13 +159,17 @@ __device__ __forceinline__ bool block_may_hit(float mx, float my, float l11, flo
 
 // Scratch of the sorted comparator (mgs_sorted.cu).
 struct SortedScratch {
-    uint64_t *nkeys, *nkeys_tmp;   // [n]   depth ranking
+    uint32_t *nkeys, *nkeys_tmp;   // [n]   depth ranking: FP32-contract depth bits
     uint32_t *nvals, *nvals_tmp;   // [n]
     uint32_t *rank;                // [n]
-    uint64_t *keys, *keys_tmp;     // [capacity] (tile, rank) keys
+    uint32_t *keys, *keys_tmp;     // [capacity] rank of each list entry
     uint32_t *vals, *vals_tmp;     // [capacity]
-    uint32_t *hist;                // [sorted_hist_entries(max(n, capacity))]
+    void *temp;                    // library sort temporary storage
+    size_t temp_bytes;
 };
+// Temporary storage the comparator's sorts need for n Gaussians, `capacity`
+// list entries and T tiles.
+size_t sorted_temp_bytes(int64_t n, int64_t capacity, int T);
 int64_t sorted_hist_entries(int64_t n_max);
 // Stable LSD radix sort of (key, value) pairs by key bits [begin_bit, end_bit).
 cudaError_t radix_sort(uint64_t **k, uint32_t **v, uint64_t **kt, uint32_t **vt, int64_t n_max,

@@ -7,10 +7,16 @@
 // stopping before the Gaussian that would bring T below 1e-4 (3DGS early
 // termination).
 //
-// Order: Gaussians are ranked by (FP32-contract view depth, index) with a
-// stable LSD radix sort of the depth bits over index-ordered input; the tile
-// lists are then sorted by (tile, rank), which keeps the tile segments the
-// counting sort produced and orders each by depth.
+// Order: Gaussians are ranked by (FP32-contract view depth, caller index)
+// with a stable radix sort of the depth bits over caller-ordered input; each
+// tile's list (a segment of the counting sort's output) is then sorted by
+// rank.  Both sorts are the CUDA library's (CUB) device radix / segmented
+// sorts, the kind of sort a sorted 3DGS renderer uses, so the comparison is
+// not made against a slow sort.  The project's own LSD radix sort below
+// serves the load-time spatial order.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_segmented_sort.cuh>
+
 #include "mgs_internal.cuh"
 
 namespace mgs {
@@ -180,14 +186,13 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
 // stable sort breaks depth ties by caller index.
 __global__ void k_depth_keys(const ProjRec *__restrict__ rec, const uint2 *__restrict__ rect,
                              const uint32_t *__restrict__ iperm, int64_t n,
-                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const uint32_t i = iperm ? iperm[j] : (uint32_t)j;
     const uint2 r = rect[i];
     const bool vis = (r.x >> 16) > (r.x & 0xFFFF);
-    const uint32_t d = vis ? __float_as_uint(rec[i].c.z) : 0xFFFFFFFFu;
-    keys[j] = (uint64_t)d << 32;
+    keys[j] = vis ? __float_as_uint(rec[i].c.z) : 0xFFFFFFFFu;   // positive floats order as uints
     vals[j] = i;
 }
 
@@ -199,14 +204,14 @@ __global__ void k_rank_scatter(const uint32_t *__restrict__ sorted_idx, int64_t 
 
 // (tile, rank) keys of every list entry; one block per tile.
 __global__ void k_tile_keys(const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ gids,
-                            const uint32_t *__restrict__ rank, int rank_bits,
-                            uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                            const DevStatus *__restrict__ status, uint64_t capacity) {
+                            const uint32_t *__restrict__ rank, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals, const DevStatus *__restrict__ status,
+                            uint64_t capacity) {
     if (status->last_pairs > capacity) return;
     const int t = blockIdx.x;
     for (uint32_t j = offsets[t] + threadIdx.x; j < offsets[t + 1]; j += blockDim.x) {
         const uint32_t g = gids[j];
-        keys[j] = ((uint64_t)t << rank_bits) | rank[g];
+        keys[j] = rank[g];
         vals[j] = g;
     }
 }
@@ -313,12 +318,6 @@ __global__ void __launch_bounds__(64) k_raster_sorted(RenderArgs args, const uin
     }
 }
 
-int bits_for(uint64_t v) {
-    int b = 0;
-    while (b < 64 && (v >> b) != 0) ++b;
-    return b;
-}
-
 }  // namespace
 
 // Sorts (key, value) pairs by bits [begin_bit, end_bit) of the key (stable
@@ -345,36 +344,46 @@ cudaError_t radix_sort(uint64_t **k, uint32_t **v, uint64_t **kt, uint32_t **vt,
 
 int64_t sorted_hist_entries(int64_t n_max) { return kRsBins * ((n_max + kRsTile - 1) / kRsTile); }
 
+size_t sorted_temp_bytes(int64_t n, int64_t capacity, int T) {
+    size_t a = 0, b = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, a, (const uint32_t *)nullptr, (uint32_t *)nullptr,
+                                    (const uint32_t *)nullptr, (uint32_t *)nullptr, (int)n);
+    cub::DeviceSegmentedSort::SortPairs(nullptr, b, (const uint32_t *)nullptr, (uint32_t *)nullptr,
+                                        (const uint32_t *)nullptr, (uint32_t *)nullptr, (int)capacity,
+                                        T, (const uint32_t *)nullptr, (const uint32_t *)nullptr);
+    return a > b ? a : b;
+}
+
 cudaError_t launch_sorted(const RenderArgs &a, const SortedScratch &s, cudaStream_t stream) {
     const int T = a.cam.tiles_x * a.cam.tiles_y;
     cudaError_t e;
-    // 1. rank the Gaussians by (view depth, index)
+    size_t tb = s.temp_bytes;
+    // 1. rank the Gaussians by (view depth, caller index): stable radix sort
+    //    of the depth bits over caller-ordered input
     if (a.n > 0) {
-        uint64_t *k = s.nkeys, *kt = s.nkeys_tmp;
-        uint32_t *v = s.nvals, *vt = s.nvals_tmp;
         k_depth_keys<<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(a.rec, a.rect, a.iperm, a.n,
-                                                                         k, v);
-        if ((e = radix_sort(&k, &v, &kt, &vt, a.n, nullptr, 32, 64, s.hist, stream)) != cudaSuccess)
+                                                                         s.nkeys, s.nvals);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cub::DeviceRadixSort::SortPairs(s.temp, tb, s.nkeys, s.nkeys_tmp, s.nvals,
+                                                 s.nvals_tmp, (int)a.n, 0, 32, stream)) != cudaSuccess)
             return e;
-        k_rank_scatter<<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(v, a.n, s.rank);
+        k_rank_scatter<<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(s.nvals_tmp, a.n, s.rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // 2. order each tile's list by rank: sort (tile, rank) keys
-    const int rb = bits_for((uint64_t)(a.n > 0 ? a.n - 1 : 0));
-    const int end_bit = rb + bits_for((uint64_t)T);
-    k_tile_keys<<<T, 128, 0, stream>>>(a.tile_offsets, a.gids, s.rank, rb, s.keys, s.vals,
-                                        a.status, a.capacity);
+    // 2. order each tile's list (a segment of the binning output) by rank
+    k_tile_keys<<<T, 128, 0, stream>>>(a.tile_offsets, a.gids, s.rank, s.keys, s.vals, a.status,
+                                        a.capacity);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    uint64_t *k = s.keys, *kt = s.keys_tmp;
-    uint32_t *v = s.vals, *vt = s.vals_tmp;
-    if ((e = radix_sort(&k, &v, &kt, &vt, (int64_t)a.capacity, &a.status->last_pairs, 0, end_bit,
-                        s.hist, stream)) != cudaSuccess)
+    tb = s.temp_bytes;
+    if ((e = cub::DeviceSegmentedSort::SortPairs(s.temp, tb, s.keys, s.keys_tmp, s.vals, s.vals_tmp,
+                                                 (int)a.capacity, T, a.tile_offsets,
+                                                 a.tile_offsets + 1, stream)) != cudaSuccess)
         return e;
     // 3. blend
     if (a.out_count)
-        k_raster_sorted<true><<<T, 64, 0, stream>>>(a, v);
+        k_raster_sorted<true><<<T, 64, 0, stream>>>(a, s.vals_tmp);
     else
-        k_raster_sorted<false><<<T, 64, 0, stream>>>(a, v);
+        k_raster_sorted<false><<<T, 64, 0, stream>>>(a, s.vals_tmp);
     return cudaGetLastError();
 }
 
