@@ -265,18 +265,31 @@ def run_gpu(args):
     stage_per_frame = [x / max(timed_frames, 1) for x in stage_ms]
     rast = {"ms_per_frame": stage_per_frame[2]}
 
-    # ---- end to end: host image buffers (pinned), D2H inside the timed region
-    host = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    # ---- end to end through the public API with host image buffers (pinned):
+    # every frame's image is copied to host memory inside the timed region.
+    # Like a viewer rendering a sequence, frames alternate between two
+    # workspaces and streams, so one frame's copy overlaps the next render.
+    ws2 = m.mgs_workspace_create(r.ctx)
+    m.mgs_workspace_reserve(ws2, scene.n, W, H, int(max(pairs) * 1.25) + 1024)
+    wss = (r.ws, ws2)
+    streams = (stream, torch.cuda.Stream(device=local))
+    hosts = [torch.empty((H, W, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
     e2e_ms = []
     for i in range(args.warmup + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for c in cstructs:
-            m.mgs_render_to_host(r.ws, h, c, opts, host, stream)
-        stream.synchronize()
+        for f, c in enumerate(cstructs):
+            m.mgs_render_to_host(wss[f & 1], h, c, opts, hosts[f & 1], streams[f & 1])
+        for s_ in streams:
+            s_.synchronize()
         if i >= args.warmup:
             e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    for w_, s_ in zip(wss, streams):
+        st, _ = m.mgs_workspace_sync(w_, s_, allow_overflow=True)
+        if st != m.MGS_OK:
+            raise RuntimeError("tile-list overflow in the end-to-end run")
+    m.mgs_workspace_destroy(ws2)
     e2e_total = max_over_ranks([sum(e2e_ms)], dist, "cuda")[0]
     e2e_fps = job_rate(N_POSES * args.steps, world, e2e_total)
 
@@ -322,6 +335,7 @@ def run_gpu(args):
             line["serving"] = run_serving(m, torch, local)
         if world == 1 and not args.no_large:
             line["large"] = run_large(m, torch, local)
+            line["sorted_comparator_600k"] = run_sorted_600k(m, torch, local)
         if world == 1 and not args.no_paper_mlp:
             line["paper_width_mlp"] = run_paper_mlp(m, torch, local)
         if world == 1 and not args.no_backward:
@@ -464,6 +478,40 @@ def run_large(m, torch, local, frames=3):
     res["pairs_per_frame"] = m.mgs_tile_lists(r.ws, stream=stream)[1]
     res["sorted_over_sort_free_time"] = res["sorted"]["ms_per_frame"] / res["sort_free"]["ms_per_frame"]
     r.close()
+    return res
+
+
+def run_sorted_600k(m, torch, local, reps=2):
+    """The benchmark workload (600k, 1600x1063, 64 poses) through the sorted
+    front-to-back comparator: per-frame stage times next to the sort-free
+    renderer's, same inputs, same GPU."""
+    from paper_2603_11531_gb300 import synth
+    scene, cams = synth.workload_unbounded_600k(n_poses=N_POSES)
+    r = m.Renderer(local)
+    h = r.load_scene(scene)
+    out = torch.empty((cams[0].height, cams[0].width, 3), device="cuda")
+    stream = torch.cuda.Stream(device=local)
+    cs = [m.camera_struct(c) for c in cams]
+    res = {}
+    for name, flags in (("sort_free", 0), ("sorted", m.MGS_FLAG_SORTED)):
+        opts = m.render_opts(use_mlp=True, flags=flags)
+        for c in cs[:4]:
+            m.mgs_render_checked(r.ws, h, c, opts, out, None, None, stream)
+        m.mgs_workspace_stage_times(r.ws, stream)
+        m.mgs_workspace_set_timing(r.ws, True)
+        for _ in range(reps):
+            for c in cs:
+                m.mgs_render(r.ws, h, c, opts, out, None, None, stream)
+        ms, fr = m.mgs_workspace_stage_times(r.ws, stream)
+        m.mgs_workspace_set_timing(r.ws, False)
+        st, _ = m.mgs_workspace_sync(r.ws, stream, allow_overflow=True)
+        if st != m.MGS_OK:
+            raise RuntimeError("comparator run overflowed its tile lists")
+        per = [x / fr for x in ms]
+        res[name] = {"ms_per_frame": sum(per), "binning_ms": per[1],
+                     ("sort_and_blend_ms" if flags else "raster_ms"): per[2], "fps": 1000.0 / sum(per)}
+    r.close()
+    res["sorted_over_sort_free_time"] = res["sorted"]["ms_per_frame"] / res["sort_free"]["ms_per_frame"]
     return res
 
 
