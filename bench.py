@@ -338,6 +338,7 @@ def run_gpu(args):
             line["sorted_comparator_600k"] = run_sorted_600k(m, torch, local)
         if world == 1 and not args.no_paper_mlp:
             line["paper_width_mlp"] = run_paper_mlp(m, torch, local)
+            line["depth_and_sh_decode"] = run_depth_and_decode(m, torch, local)
         if world == 1 and not args.no_backward:
             line["backward"] = run_backward(m, torch, local)
         if world == 1 and not args.no_cpu_baseline:
@@ -513,6 +514,49 @@ def run_sorted_600k(m, torch, local, reps=2):
     r.close()
     res["sorted_over_sort_free_time"] = res["sorted"]["ms_per_frame"] / res["sort_free"]["ms_per_frame"]
     return res
+
+
+def run_depth_and_decode(m, torch, local, reps=2):
+    """The 600k workload's depth image (Eq. 5, mgs_render_depth, FP32 sums)
+    per frame, and the load-time SH decode of Eq. 6 (mgs_decode_sh) of the
+    600k scene's features."""
+    from paper_2603_11531_gb300 import synth
+    scene, cams = synth.workload_unbounded_600k(n_poses=N_POSES)
+    r = m.Renderer(local)
+    h = r.load_scene(scene)
+    H, W = cams[0].height, cams[0].width
+    rgb = torch.empty((H, W, 3), device="cuda")
+    depth = torch.empty((H, W), device="cuda")
+    stream = torch.cuda.Stream(device=local)
+    opts = m.render_opts(use_mlp=True)
+    cs = [m.camera_struct(c) for c in cams]
+    for c in cs[:4]:
+        m.mgs_render_depth(r.ws, h, c, opts, rgb, depth, stream)
+        m.mgs_workspace_sync(r.ws, stream, allow_overflow=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        for c in cs:
+            m.mgs_render_depth(r.ws, h, c, opts, rgb, depth, stream)
+    e1.record(stream)
+    e1.synchronize()
+    depth_ms = e0.elapsed_time(e1) / (reps * len(cs))
+    st, _ = m.mgs_workspace_sync(r.ws, stream, allow_overflow=True)
+    if st != m.MGS_OK:
+        raise RuntimeError("depth run overflowed its tile lists")
+    md, mv = synth.random_sh_decoders(7)
+    hfeat = torch.from_numpy(synth.compressed_sh_features(scene.n, seed=8, precision="fp16")).cuda()
+    attrs = torch.from_numpy(scene.attrs.copy()).cuda()
+    for _ in range(3):
+        m.mgs_decode_sh(r.ctx, hfeat, md, mv, attrs, stream)
+    e0.record(stream)
+    for _ in range(10):
+        m.mgs_decode_sh(r.ctx, hfeat, md, mv, attrs, stream)
+    e1.record(stream)
+    e1.synchronize()
+    r.close()
+    return {"depth_render_ms_per_frame": depth_ms, "depth_render_fps": 1000.0 / depth_ms,
+            "sh_decode_ms_600k": e0.elapsed_time(e1) / 10}
 
 
 def run_paper_mlp(m, torch, local, reps=2):
