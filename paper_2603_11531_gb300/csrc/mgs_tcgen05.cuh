@@ -93,6 +93,19 @@ __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// 16 consecutive FP32 columns of this thread's TMEM lane, without waiting.
+__device__ __forceinline__ void ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void ld_wait() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // 16 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
@@ -348,7 +361,8 @@ __device__ __forceinline__ bool layer(unsigned char *base, const WideLayout &L, 
     return ok;
 }
 
-// BF16(ReLU(D + b)) of this thread's row into the next A operand (K = N).
+// BF16(ReLU(D + b)) of this thread's row into the next A operand (K = N):
+// 64 columns per TMEM wait, each 8-column core-matrix row one 16-byte store.
 __device__ __forceinline__ void relu_to_bf16(unsigned char *base, const WideLayout &L,
                                              uint32_t bias_off, uint32_t out_off, int N) {
     const uint32_t tmem = *reinterpret_cast<const uint32_t *>(base + L.tmem);
@@ -356,14 +370,30 @@ __device__ __forceinline__ void relu_to_bf16(unsigned char *base, const WideLayo
     const float *b = reinterpret_cast<const float *>(base + bias_off);
     const int row = threadIdx.x;
 #pragma unroll 1
-    for (int c = 0; c < N; c += 16) {
-        float v[16];
-        tc::ld16(lane0 + (uint32_t)c, v);
+    for (int c0 = 0; c0 < N; c0 += 64) {
+        uint32_t r[4][16];
 #pragma unroll
-        for (int i = 0; i < 16; i += 2)
-            tc::store_bf16x2(reinterpret_cast<__nv_bfloat16 *>(base + out_off),
-                             tc::core_off(row, c + i, N), fmaxf(v[i] + b[c + i], 0.0f),
-                             fmaxf(v[i + 1] + b[c + i + 1], 0.0f));
+        for (int q = 0; q < 4; ++q)
+            if (c0 + 16 * q < N) tc::ld16_nowait(lane0 + (uint32_t)(c0 + 16 * q), r[q]);
+        tc::ld_wait();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (c0 + 16 * q >= N) break;
+#pragma unroll
+            for (int h = 0; h < 16; h += 8) {
+                const int c = c0 + 16 * q + h;
+                uint4 u;
+                uint32_t *w = &u.x;
+#pragma unroll
+                for (int i = 0; i < 8; i += 2) {
+                    const __nv_bfloat162 p =
+                        __floats2bfloat162_rn(fmaxf(__uint_as_float(r[q][h + i]) + b[c + i], 0.0f),
+                                              fmaxf(__uint_as_float(r[q][h + i + 1]) + b[c + i + 1], 0.0f));
+                    w[i / 2] = *reinterpret_cast<const uint32_t *>(&p);
+                }
+                *reinterpret_cast<uint4 *>(base + out_off + tc::core_off(row, c, N)) = u;
+            }
+        }
     }
 }
 
@@ -405,14 +435,23 @@ __device__ __forceinline__ bool mlp_cta(unsigned char *base, const WideLayout &L
 #pragma unroll
     for (int k = 0; k < kMlpOut; ++k) acc[k] = b4[k];
 #pragma unroll 1
-    for (int c = 0; c < h3; c += 16) {
-        float v[16];
-        tc::ld16(lane0 + (uint32_t)c, v);
+    for (int c0 = 0; c0 < h3; c0 += 64) {
+        uint32_t r[4][16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(v[i] + b3[c + i], 0.0f)));
+        for (int q = 0; q < 4; ++q)
+            if (c0 + 16 * q < h3) tc::ld16_nowait(lane0 + (uint32_t)(c0 + 16 * q), r[q]);
+        tc::ld_wait();
 #pragma unroll
-            for (int k = 0; k < kMlpOut; ++k) acc[k] = fmaf(head[k * h3 + c + i], h, acc[k]);
+        for (int q = 0; q < 4; ++q) {
+            if (c0 + 16 * q >= h3) break;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int c = c0 + 16 * q + i;
+                const float h =
+                    __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(r[q][i]) + b3[c], 0.0f)));
+#pragma unroll
+                for (int k = 0; k < kMlpOut; ++k) acc[k] = fmaf(head[k * h3 + c], h, acc[k]);
+            }
         }
     }
 #pragma unroll
