@@ -312,6 +312,9 @@ def run_gpu(args):
             "config": {"workload": "unbounded_600k_fp16_mlp_1600x1063_orbit64",
                        "gaussians": scene.n, "resolution": [W, H], "poses_per_step": N_POSES,
                        "attrs": "fp16", "mlp": "bf16 22-64-64-5", "parallelism": "replicas",
+                       "arith": ("FP32 projection, inclusion test, alpha and T; A and B sums on "
+                                 "tensor cores (FP16 alpha x FP16 high+low weights, FP32 "
+                                 "accumulate); BF16 MLP on tcgen05"),
                        "l2": "flushed (512 MB write) between timed steps",
                        "pairs_per_frame_mean": sum(pairs) / len(pairs),
                        "hits_per_frame_mean": mean_hits},
