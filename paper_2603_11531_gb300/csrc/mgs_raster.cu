@@ -218,10 +218,10 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
 // ---------------------------------------------------------------------------
 // Tensor-core accumulation of A and B (FP16-attribute scenes).
 //
-// One CTA (four warps) per tile; warp w owns the 16x4 block of rows
-// 4w..4w+3.  A warp's 64 pixels are the M = 64 rows of four m16n8k8 tiles:
-// lane (g, t) = (lane / 4, lane % 4) owns the eight pixels
-// x = 8 (g / 4) + 0..7 of row g % 4 (rows g and g + 8 of m-tile i are
+// One CTA (four warps) per tile; warp w owns the 8x8 block at
+// (8 (w % 2), 8 (w / 2)) of the tile.  A warp's 64 pixels are the M = 64 rows
+// of four m16n8k8 tiles: lane (g, t) = (lane / 4, lane % 4) owns the eight
+// pixels x = 0..7 of the block's row g (rows g and g + 8 of m-tile i are
 // pixels 2i and 2i + 1), shared by the four lanes of its quad.  Candidates
 // are gathered into chunks of 8 Gaussians (the K dimension); lane t of a
 // quad evaluates chunk entries 2t and 2t + 1 at its pixels -- one packed
@@ -310,16 +310,16 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
-    const int bx0 = tx * kTile, by0 = ty * kTile + 4 * warp;
-    const int xb = bx0 + 8 * (g >> 2);
-    const int py = by0 + (g & 3);
+    const int bx0 = tx * kTile + 8 * (warp & 1), by0 = ty * kTile + 8 * (warp >> 1);
+    const int xb = bx0;
+    const int py = by0 + g;
     float4(*geo)[kRing / 2] = sm.geo[warp];
     uint4 *wt = sm.wt[warp];
 
     const uint32_t start = args.tile_offsets[tile];
     const uint32_t end = args.tile_offsets[tile + 1];
     const bool no_cull = (args.flags & MGS_FLAG_NO_CULL) != 0;
-    const float bcx = (float)bx0 + 8.0f, bcy = (float)by0 + 2.0f;
+    const float bcx = (float)bx0 + 4.0f, bcy = (float)by0 + 4.0f;
     // weight scale 2^(14 - e) when the frame's largest weight has exponent e >= 14
     const int we = (int)((args.status->wmax_frame_bits >> 23) & 0xFFu) - 127;
     const float wscale = we >= 14 ? __int_as_float((127 + 14 - we) << 23) : 1.0f;
@@ -360,7 +360,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
         const float2 b = b_n;
         const uint4 wv = w_n;
         const bool cand =
-            j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bcx, bcy, 7.5f, 1.5f));
+            j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bcx, bcy, 3.5f, 3.5f));
         if (j + 32 < end) {
             const uint32_t gid = __ldg(&args.gids[j + 32]);
             a_n = __ldg(&args.rec[gid].a);
