@@ -14,9 +14,11 @@
 //                     warp and added to a per-Gaussian gradient record.
 //   k_preprocess_bwd  one thread per Gaussian: recomputes the forward, chains
 //                     through the EWA covariance, projection, SH colour,
-//                     Eq. 3 weight and (warp-cooperatively) the Eq. 4 MLP; MLP
-//                     weight gradients are summed per CTA, then reduced in a
-//                     fixed order by k_mlp_grad_reduce.
+//                     Eq. 3 weight and (warp-cooperatively) the Eq. 4 MLP.
+//                     The MLP's deltas and weight gradients are TF32 mma.sync
+//                     products (FP32 accumulation); weight gradients stay in
+//                     registers across the CTA's rows, are written once per
+//                     CTA and reduced in a fixed order by k_mlp_grad_reduce.
 #include "mgs_internal.cuh"
 #include "mgs_mlp.cuh"
 
@@ -185,24 +187,170 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
 // Preprocessing adjoint.
 // ---------------------------------------------------------------------------
 
-constexpr int kDStride = 65;  // floats per per-row delta buffer (conflict-free)
 constexpr int kMlpGrad = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden +
                          kMlpHidden + kMlpOut * kMlpHidden + kMlpOut;  // 5957
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kMlpHidden * kMlpIn, kOffW2 = kOffB1 + kMlpHidden,
               kOffB2 = kOffW2 + kMlpHidden * kMlpHidden, kOffW3 = kOffB2 + kMlpHidden,
               kOffB3 = kOffW3 + kMlpOut * kMlpHidden;
 
+// Row buffers of the MLP adjoint hold the CTA's 128 rows (row = warp * 32 +
+// lane).  Strides: 72 floats per delta row make the transposed fragment
+// loads of the weight-gradient products conflict-free; 8 per d3 row and 24
+// per staged dx row.
+constexpr int kRows = kMlpThreads;
+constexpr int kDS = 72;
+constexpr int kD3S = 8;
+constexpr int kDxS = 24;
+constexpr int kOnesCol = kMlpHidden;  // h1 column 64 holds 1: its products give dL/db2
+constexpr int kXOnesCol = kMlpIn;     // x column 22 holds 1: its products give dL/db1
+
 struct BwdSmem {
-    MlpSmem mlp;
-    __nv_bfloat16 h1[kMlpThreads / 32][32 * kHStride];
-    __nv_bfloat16 h2[kMlpThreads / 32][32 * kHStride];
-    float d2[kMlpThreads / 32][32 * kDStride];
-    float d1[kMlpThreads / 32][32 * kDStride];
-    float d3[kMlpThreads / 32][32 * 8];
-    float acc[kMlpGrad];
+    MlpSmem mlp;                          // weights, BF16 features x, head outputs
+    __nv_bfloat16 h1[kRows * kHStride];   // BF16 hidden activations (forward recompute)
+    __nv_bfloat16 h2[kRows * kHStride];
+    float d2[kRows * kDS];                // dL/d(pre-activation 2)
+    float d1[kRows * kDS];                // dL/d(pre-activation 1)
+    float d3[kRows * kD3S];               // dL/d(head outputs), columns 5..7 zero
+    float dx[kRows * kDxS];               // dL/d(features), staged for the row threads
+    float b3[kMlpThreads / 32][8];        // per-warp sums of d3
 };
 
-__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+// Weight-gradient accumulators of one lane (m16n8 fragments): warp w owns
+// rows 16w..16w+15 of dW2 (nine n-tiles, the last one the b2 column), of dW1
+// (three n-tiles; column 22 is b1) and of dW3^T.
+struct WGradAcc {
+    float w2[9][4];
+    float w1[3][4];
+    float w3[4];
+};
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// A BF16 value as a TF32 operand (exact: BF16 keeps 8 significand bits).
+__device__ __forceinline__ uint32_t bf_tf32(const __nv_bfloat16 *p) {
+    return (uint32_t)(*reinterpret_cast<const unsigned short *>(p)) << 16;
+}
+// D += A B, m16n8k8, TF32 operands, FP32 accumulation.  Fragments (g = lane / 4,
+// t = lane % 4): a = A[g][t], A[g+8][t], A[g][t+4], A[g+8][t+4]; b = B[t][g],
+// B[t+4][g]; d = D[g][2t], D[g][2t+1], D[g+8][2t], D[g+8][2t+1].
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float2 relu_mask(const __nv_bfloat16 *h, float a, float b) {
+    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(h);
+    return make_float2(__low2float(m) > 0.0f ? a : 0.0f, __high2float(m) > 0.0f ? b : 0.0f);
+}
+
+// Deltas of the Eq. 4 MLP for the warp's 32 rows (d3 already in shared
+// memory):  d2 = (d3 W3) * [h2 > 0],  d1 = (d2 W2) * [h1 > 0],  dx = d1 W1.
+// d2 and d1 stay in shared memory for the weight gradients; dx is staged for
+// the row threads.  The d1 accumulators serve directly as the A fragments of
+// dx = d1 W1, taking k = 2t and 2t + 1 of each step for fragment columns t
+// and t + 4 (B rows follow the same order).
+__device__ __forceinline__ void mlp_deltas_warp(BwdSmem &sm, int warp, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = warp * 32 + mt * 16 + g, r1 = r0 + 8;
+        {
+            const uint32_t a0 = to_tf32(sm.d3[r0 * kD3S + t]), a1 = to_tf32(sm.d3[r1 * kD3S + t]);
+            const uint32_t a2 = to_tf32(sm.d3[r0 * kD3S + t + 4]);
+            const uint32_t a3 = to_tf32(sm.d3[r1 * kD3S + t + 4]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_tf32(c, a0, a1, a2, a3, bf_tf32(&sm.mlp.w3[t * kW2Stride + nt * 8 + g]),
+                         bf_tf32(&sm.mlp.w3[(t + 4) * kW2Stride + nt * 8 + g]));
+                const int col = nt * 8 + 2 * t;
+                *reinterpret_cast<float2 *>(&sm.d2[r0 * kDS + col]) =
+                    relu_mask(&sm.h2[r0 * kHStride + col], c[0], c[1]);
+                *reinterpret_cast<float2 *>(&sm.d2[r1 * kDS + col]) =
+                    relu_mask(&sm.h2[r1 * kHStride + col], c[2], c[3]);
+            }
+        }
+        __syncwarp();
+        float c[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+            const int k0 = ks * 8;
+            const uint32_t a0 = to_tf32(sm.d2[r0 * kDS + k0 + t]);
+            const uint32_t a1 = to_tf32(sm.d2[r1 * kDS + k0 + t]);
+            const uint32_t a2 = to_tf32(sm.d2[r0 * kDS + k0 + t + 4]);
+            const uint32_t a3 = to_tf32(sm.d2[r1 * kDS + k0 + t + 4]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+                mma_tf32(c[nt], a0, a1, a2, a3, bf_tf32(&sm.mlp.w2[(k0 + t) * kW2Stride + nt * 8 + g]),
+                         bf_tf32(&sm.mlp.w2[(k0 + t + 4) * kW2Stride + nt * 8 + g]));
+        }
+        float dx[3][4];
+#pragma unroll
+        for (int ft = 0; ft < 3; ++ft) dx[ft][0] = dx[ft][1] = dx[ft][2] = dx[ft][3] = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int col = nt * 8 + 2 * t;
+            const float2 e0 = relu_mask(&sm.h1[r0 * kHStride + col], c[nt][0], c[nt][1]);
+            const float2 e1 = relu_mask(&sm.h1[r1 * kHStride + col], c[nt][2], c[nt][3]);
+            *reinterpret_cast<float2 *>(&sm.d1[r0 * kDS + col]) = e0;
+            *reinterpret_cast<float2 *>(&sm.d1[r1 * kDS + col]) = e1;
+            const uint32_t a0 = to_tf32(e0.x), a1 = to_tf32(e1.x), a2 = to_tf32(e0.y),
+                           a3 = to_tf32(e1.y);
+#pragma unroll
+            for (int ft = 0; ft < 3; ++ft)
+                mma_tf32(dx[ft], a0, a1, a2, a3, bf_tf32(&sm.mlp.w1[col * kW1Stride + ft * 8 + g]),
+                         bf_tf32(&sm.mlp.w1[(col + 1) * kW1Stride + ft * 8 + g]));
+        }
+#pragma unroll
+        for (int ft = 0; ft < 3; ++ft) {
+            const int col = ft * 8 + 2 * t;
+            *reinterpret_cast<float2 *>(&sm.dx[r0 * kDxS + col]) = make_float2(dx[ft][0], dx[ft][1]);
+            *reinterpret_cast<float2 *>(&sm.dx[r1 * kDxS + col]) = make_float2(dx[ft][2], dx[ft][3]);
+        }
+    }
+}
+
+// Adds the weight gradients of the CTA's 128 rows to this lane's
+// accumulators: dW2 = d2^T [h1 | 1], dW1 = d1^T [x | 1], dW3^T = h2^T d3,
+// each a sum over the rows (the K dimension), warp w taking output rows
+// 16w..16w+15.
+__device__ __forceinline__ void mlp_wgrad_cta(const BwdSmem &sm, int warp, int lane, WGradAcc &acc) {
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = warp * 16 + g, m1 = m0 + 8;
+    const __nv_bfloat16 *X = &sm.mlp.x[0][0];
+#pragma unroll 2
+    for (int ks = 0; ks < kRows / 8; ++ks) {
+        const int ra = ks * 8 + t, rb = ra + 4;
+        {
+            const uint32_t a0 = to_tf32(sm.d2[ra * kDS + m0]), a1 = to_tf32(sm.d2[ra * kDS + m1]);
+            const uint32_t a2 = to_tf32(sm.d2[rb * kDS + m0]), a3 = to_tf32(sm.d2[rb * kDS + m1]);
+#pragma unroll
+            for (int nt = 0; nt < 9; ++nt)
+                mma_tf32(acc.w2[nt], a0, a1, a2, a3, bf_tf32(&sm.h1[ra * kHStride + nt * 8 + g]),
+                         bf_tf32(&sm.h1[rb * kHStride + nt * 8 + g]));
+        }
+        {
+            const uint32_t a0 = to_tf32(sm.d1[ra * kDS + m0]), a1 = to_tf32(sm.d1[ra * kDS + m1]);
+            const uint32_t a2 = to_tf32(sm.d1[rb * kDS + m0]), a3 = to_tf32(sm.d1[rb * kDS + m1]);
+#pragma unroll
+            for (int ft = 0; ft < 3; ++ft)
+                mma_tf32(acc.w1[ft], a0, a1, a2, a3, bf_tf32(&X[ra * kXStride + ft * 8 + g]),
+                         bf_tf32(&X[rb * kXStride + ft * 8 + g]));
+        }
+        mma_tf32(acc.w3, bf_tf32(&sm.h2[ra * kHStride + m0]), bf_tf32(&sm.h2[ra * kHStride + m1]),
+                 bf_tf32(&sm.h2[rb * kHStride + m0]), bf_tf32(&sm.h2[rb * kHStride + m1]),
+                 to_tf32(sm.d3[ra * kD3S + g]), to_tf32(sm.d3[rb * kD3S + g]));
+    }
+}
 
 template <bool kFP16>
 __device__ __forceinline__ void load_rec(const void *attrs, int64_t i, float (&v)[kRec]) {
@@ -243,8 +391,21 @@ __global__ void __launch_bounds__(kMlpThreads) k_preprocess_bwd(RenderArgs args,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if constexpr (kMLP) {
         mlp_load_weights(sm.mlp, args.mlp);
-        for (int e = threadIdx.x; e < kMlpGrad; e += blockDim.x) sm.acc[e] = 0.f;
-        __syncthreads();
+        // h1 columns 64..71: a column of ones (bias gradient b2), then zeros
+        for (int e = threadIdx.x; e < kRows * 8; e += blockDim.x)
+            sm.h1[(e >> 3) * kHStride + kOnesCol + (e & 7)] =
+                __float2bfloat16((e & 7) == 0 ? 1.0f : 0.0f);
+    }
+    WGradAcc wacc;
+    float sb3[kMlpOut];
+    if constexpr (kMLP) {
+#pragma unroll
+        for (int nt = 0; nt < 9; ++nt) wacc.w2[nt][0] = wacc.w2[nt][1] = wacc.w2[nt][2] = wacc.w2[nt][3] = 0.f;
+#pragma unroll
+        for (int ft = 0; ft < 3; ++ft) wacc.w1[ft][0] = wacc.w1[ft][1] = wacc.w1[ft][2] = wacc.w1[ft][3] = 0.f;
+        wacc.w3[0] = wacc.w3[1] = wacc.w3[2] = wacc.w3[3] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMlpOut; ++k) sb3[k] = 0.f;
     }
     const float *W = cam.R;
     float cc[3];
@@ -256,6 +417,8 @@ __global__ void __launch_bounds__(kMlpThreads) k_preprocess_bwd(RenderArgs args,
 
     for (int64_t base = (int64_t)blockIdx.x * kMlpThreads; base < args.n;
          base += (int64_t)gridDim.x * kMlpThreads) {
+        // the previous iteration's weight-gradient products read every warp's rows
+        if constexpr (kMLP) __syncthreads();
         const int64_t i = base + threadIdx.x;
         const bool valid = i < args.n;
         float v[kRec];
@@ -292,6 +455,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_preprocess_bwd(RenderArgs args,
 #pragma unroll
                 for (int k = 0; k < 12; ++k) f[10 + k] = v[11 + k];
             }
+            f[kXOnesCol] = 1.0f;  // W1's column 22 is zero: the forward is unchanged
 #pragma unroll
             for (int k = 0; k < kMlpK1; k += 8) {
                 uint4 u;
@@ -302,7 +466,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_preprocess_bwd(RenderArgs args,
                 *reinterpret_cast<uint4 *>(xr + k) = u;
             }
             __syncwarp();
-            mlp_warp<true>(sm.mlp, warp, lane, sm.h1[warp], sm.h2[warp]);
+            mlp_warp<true>(sm.mlp, warp, lane, sm.h1 + warp * 32 * kHStride, sm.h2 + warp * 32 * kHStride);
             __syncwarp();
 #pragma unroll
             for (int k = 0; k < 5; ++k) yv[k] = sm.mlp.out[warp][lane][k];
@@ -443,100 +607,24 @@ __global__ void __launch_bounds__(kMlpThreads) k_preprocess_bwd(RenderArgs args,
             d3[3] = kResidual ? dbase[1] : 0.0f;
             d3[4] = kResidual ? dbase[2] : 0.0f;
             if (!vis) d3[0] = d3[1] = d3[2] = d3[3] = d3[4] = 0.0f;
+            const int row = warp * 32 + lane;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) sm.d3[warp][lane * 8 + k] = d3[k];
-            const __nv_bfloat16 *h1 = &sm.h1[warp][lane * kHStride];
-            const __nv_bfloat16 *h2 = &sm.h2[warp][lane * kHStride];
-            float *d2 = &sm.d2[warp][lane * kDStride];
-            float *d1 = &sm.d1[warp][lane * kDStride];
-            for (int jj = 0; jj < kMlpHidden; ++jj) {
-                float acc = 0.f;
+            for (int k = 0; k < 8; ++k) sm.d3[row * kD3S + k] = k < kMlpOut ? d3[k] : 0.0f;
 #pragma unroll
-                for (int k = 0; k < 5; ++k) acc += bf(sm.mlp.w3[k * kW2Stride + jj]) * d3[k];
-                d2[jj] = bf(h2[jj]) > 0.0f ? acc : 0.0f;
-            }
-            float dh1[kMlpHidden];
-#pragma unroll
-            for (int ii = 0; ii < kMlpHidden; ++ii) dh1[ii] = 0.f;
-            for (int jj = 0; jj < kMlpHidden; ++jj) {
-                const float dj = d2[jj];
-                const __nv_bfloat16 *wr = &sm.mlp.w2[jj * kW2Stride];
-#pragma unroll
-                for (int ii = 0; ii < kMlpHidden; ++ii) dh1[ii] += bf(wr[ii]) * dj;
-            }
-            float dx[kMlpIn];
-#pragma unroll
-            for (int f = 0; f < kMlpIn; ++f) dx[f] = 0.f;
-#pragma unroll
-            for (int ii = 0; ii < kMlpHidden; ++ii) {
-                const float di = bf(h1[ii]) > 0.0f ? dh1[ii] : 0.0f;
-                d1[ii] = di;
-                const __nv_bfloat16 *wr = &sm.mlp.w1[ii * kW1Stride];
-#pragma unroll
-                for (int f = 0; f < kMlpIn; ++f) dx[f] += bf(wr[f]) * di;
-            }
+            for (int k = 0; k < kMlpOut; ++k) sb3[k] += d3[k];
             __syncwarp();
-            // weight gradients of this warp's 32 rows -> CTA accumulators
-            {
-                const int j0 = 2 * lane;
-                float a2[2][kMlpHidden];
+            mlp_deltas_warp(sm, warp, lane);
+            __syncthreads();
+            mlp_wgrad_cta(sm, warp, lane, wacc);
+            float dx[kDxS];
 #pragma unroll
-                for (int ii = 0; ii < kMlpHidden; ++ii) a2[0][ii] = a2[1][ii] = 0.f;
-                float a1[2][kMlpIn];
-#pragma unroll
-                for (int f = 0; f < kMlpIn; ++f) a1[0][f] = a1[1][f] = 0.f;
-                float a3[5][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-                float sb1[2] = {0.f, 0.f}, sb2[2] = {0.f, 0.f}, sb3 = 0.f;
-                for (int r = 0; r < 32; ++r) {
-                    const float e0 = sm.d2[warp][r * kDStride + j0];
-                    const float e1 = sm.d2[warp][r * kDStride + j0 + 1];
-                    const float f0 = sm.d1[warp][r * kDStride + j0];
-                    const float f1 = sm.d1[warp][r * kDStride + j0 + 1];
-                    const __nv_bfloat16 *h1r = &sm.h1[warp][r * kHStride];
-                    const __nv_bfloat16 *xr = &sm.mlp.x[warp][r * kXStride];
-#pragma unroll
-                    for (int ii = 0; ii < kMlpHidden; ++ii) {
-                        const float hv = bf(h1r[ii]);
-                        a2[0][ii] += e0 * hv;
-                        a2[1][ii] += e1 * hv;
-                    }
-#pragma unroll
-                    for (int f = 0; f < kMlpIn; ++f) {
-                        const float xv = bf(xr[f]);
-                        a1[0][f] += f0 * xv;
-                        a1[1][f] += f1 * xv;
-                    }
-                    const float h20 = bf(sm.h2[warp][r * kHStride + j0]);
-                    const float h21 = bf(sm.h2[warp][r * kHStride + j0 + 1]);
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        const float dk = sm.d3[warp][r * 8 + k];
-                        a3[k][0] += dk * h20;
-                        a3[k][1] += dk * h21;
-                    }
-                    sb1[0] += f0;
-                    sb1[1] += f1;
-                    sb2[0] += e0;
-                    sb2[1] += e1;
-                    if (lane < 5) sb3 += sm.d3[warp][r * 8 + lane];
-                }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                    for (int ii = 0; ii < kMlpHidden; ++ii)
-                        atomicAdd(&sm.acc[kOffW2 + (j0 + h) * kMlpHidden + ii], a2[h][ii]);
-#pragma unroll
-                    for (int f = 0; f < kMlpIn; ++f)
-                        atomicAdd(&sm.acc[kOffW1 + (j0 + h) * kMlpIn + f], a1[h][f]);
-#pragma unroll
-                    for (int k = 0; k < 5; ++k)
-                        atomicAdd(&sm.acc[kOffW3 + k * kMlpHidden + j0 + h], a3[k][h]);
-                    atomicAdd(&sm.acc[kOffB1 + j0 + h], sb1[h]);
-                    atomicAdd(&sm.acc[kOffB2 + j0 + h], sb2[h]);
-                }
-                if (lane < 5) atomicAdd(&sm.acc[kOffB3 + lane], sb3);
+            for (int k = 0; k < kDxS; k += 4) {
+                const float4 q4 = *reinterpret_cast<const float4 *>(&sm.dx[row * kDxS + k]);
+                dx[k] = q4.x;
+                dx[k + 1] = q4.y;
+                dx[k + 2] = q4.z;
+                dx[k + 3] = q4.w;
             }
-            __syncwarp();
             dP[0] += dx[0];
             dP[1] += dx[1];
             dP[2] += dx[2];
@@ -596,9 +684,57 @@ __global__ void __launch_bounds__(kMlpThreads) k_preprocess_bwd(RenderArgs args,
         out[23] = 0.f;
     }
     if constexpr (kMLP) {
+        // every element of this CTA's partial row is owned by one (lane, register)
+        float *P = partials + (size_t)blockIdx.x * kMlpGrad;
+        const int g = lane >> 2, t = lane & 3;
+        const int m0 = warp * 16 + g, m1 = m0 + 8;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int c = nt * 8 + 2 * t;
+            P[kOffW2 + m0 * kMlpHidden + c] = wacc.w2[nt][0];
+            P[kOffW2 + m0 * kMlpHidden + c + 1] = wacc.w2[nt][1];
+            P[kOffW2 + m1 * kMlpHidden + c] = wacc.w2[nt][2];
+            P[kOffW2 + m1 * kMlpHidden + c + 1] = wacc.w2[nt][3];
+        }
+        if (t == 0) {
+            P[kOffB2 + m0] = wacc.w2[8][0];
+            P[kOffB2 + m1] = wacc.w2[8][2];
+        }
+#pragma unroll
+        for (int ft = 0; ft < 3; ++ft) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int f = ft * 8 + 2 * t + h;
+                if (f < kMlpIn) {
+                    P[kOffW1 + m0 * kMlpIn + f] = wacc.w1[ft][h];
+                    P[kOffW1 + m1 * kMlpIn + f] = wacc.w1[ft][2 + h];
+                } else if (f == kXOnesCol) {
+                    P[kOffB1 + m0] = wacc.w1[ft][h];
+                    P[kOffB1 + m1] = wacc.w1[ft][2 + h];
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * t + h;
+            if (k < kMlpOut) {
+                P[kOffW3 + k * kMlpHidden + m0] = wacc.w3[h];
+                P[kOffW3 + k * kMlpHidden + m1] = wacc.w3[2 + h];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kMlpOut; ++k) {
+            float x = sb3[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) sm.b3[warp][k] = x;
+        }
         __syncthreads();
-        for (int e = threadIdx.x; e < kMlpGrad; e += blockDim.x)
-            partials[(size_t)blockIdx.x * kMlpGrad + e] = sm.acc[e];
+        if (threadIdx.x < kMlpOut) {
+            float x = 0.f;
+            for (int w = 0; w < kMlpThreads / 32; ++w) x += sm.b3[w][threadIdx.x];
+            P[kOffB3 + threadIdx.x] = x;
+        }
     }
 }
 
