@@ -54,34 +54,32 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
     const int py = by0 + (lane >> 2);
     if (args.status->last_pairs > args.capacity) return;
 
-    // per-pixel constants from the forward's (A, B, T) and dL/dC
+    // per-pixel constants from the forward's (A, B, T) and dL/dC, with
+    // k_A = (1 - T) / B and r = A / B:  kG = k_A G,  kGr = k_A G.r,
+    // TGb = T G.(c_bg - r)  (all zero for pixels without coverage)
     const int64_t HW = (int64_t)cam.width * cam.height;
-    float G[4][3], kA[4], Gr[4], Gbr[4], Tp[4];
-    bool valid[4];
+    float kG[4][3], kGr[4], TGb[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int x = px0 + k;
-        valid[k] = false;
-        G[k][0] = G[k][1] = G[k][2] = 0.f;
-        kA[k] = Gr[k] = Gbr[k] = Tp[k] = 0.f;
+        kG[k][0] = kG[k][1] = kG[k][2] = kGr[k] = TGb[k] = 0.f;
         if (x < cam.width && py < cam.height) {
             const int64_t p = (int64_t)py * cam.width + x;
             const float B = aux[3 * HW + p];
             if (B > 0.0f) {
                 const float T = aux[4 * HW + p];
                 const float inv = 1.0f / B;
-                float r[3];
+                const float kA = (1.0f - T) * inv;
+                float G[3], r[3];
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    G[k][ch] = dL[3 * p + ch];
+                    G[ch] = dL[3 * p + ch];
                     r[ch] = aux[ch * HW + p] * inv;
+                    kG[k][ch] = kA * G[ch];
                 }
-                kA[k] = (1.0f - T) * inv;
-                Gr[k] = G[k][0] * r[0] + G[k][1] * r[1] + G[k][2] * r[2];
-                Gbr[k] = G[k][0] * (args.bg[0] - r[0]) + G[k][1] * (args.bg[1] - r[1]) +
-                         G[k][2] * (args.bg[2] - r[2]);
-                Tp[k] = T;
-                valid[k] = true;
+                kGr[k] = kA * (G[0] * r[0] + G[1] * r[1] + G[2] * r[2]);
+                TGb[k] = T * (G[0] * (args.bg[0] - r[0]) + G[1] * (args.bg[1] - r[1]) +
+                              G[2] * (args.bg[2] - r[2]));
             }
         }
     }
@@ -121,13 +119,17 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
         for (int k0 = 0; k0 < nc; k0 += kRedGroup) {
         const int ng = min(kRedGroup, nc - k0);
         for (int k = k0; k < k0 + ng; ++k) {
-            const float4 s0 = wb[0][k], s1 = wb[1][k], s2 = wb[2][k], s3 = wb[3][k];
-            const float mx = s0.x, my = s0.y, l11 = s0.z, l21 = s0.w;
-            const float l22 = s1.x, lo = s1.y, io = s1.z, w = s1.w;
-            const float cr = s2.x, cg = s2.y, cb = s2.z, cA = s2.w, cB = s3.x, cC = s3.y;
-            float acc[10];
-#pragma unroll
-            for (int e = 0; e < 10; ++e) acc[e] = 0.f;
+            const float4 cs0 = wb[0][k], cs1 = wb[1][k], cs2 = wb[2][k], cs3 = wb[3][k];
+            const float mx = cs0.x, my = cs0.y, l11 = cs0.z, l21 = cs0.w;
+            const float l22 = cs1.x, lo = cs1.y, io = cs1.z, w = cs1.w;
+            const float cr = cs2.x, cg = cs2.y, cb = cs2.z, cA = cs2.w, cB = cs3.x, cC = cs3.y;
+            // per pixel with q <= 9 (a = min(a_raw, 0.99), u = k_A (G.c - G.r)):
+            //   dc  += w a kG          dw += a u
+            // and, where the clamp is inactive, with s = a (w u - TGb / (1 - a)):
+            //   do  += s / o,  and s, s dx, s dx^2 for the mean and conic terms
+            // (dy is the same for the lane's four pixels)
+            float sc0 = 0.f, sc1 = 0.f, sc2 = 0.f, sw = 0.f;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
             const float dy = __fsub_rn(pyc, my);
             const float ldy = __fmul_rn(l21, dy);
             const float e2 = __fmul_rn(l22, dy);
@@ -137,26 +139,39 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
                 const float dx = __fsub_rn((float)(px0 + px) + 0.5f, mx);
                 const float e1 = __fmaf_rn(l11, dx, ldy);
                 const float q = __fmaf_rn(e1, e1, e2s);
-                if (!valid[px] || !(q <= 9.0f)) continue;
+                if (!(q <= 9.0f)) continue;
                 const float araw = ex2f(__fmaf_rn(q, kq, lo));
                 const float al = fminf(araw, 0.99f);
-                const float Gc = G[px][0] * cr + G[px][1] * cg + G[px][2] * cb;
-                // 1 - al >= 0.01: the fast reciprocal division is accurate to a few ulp
-                const float gal = w * kA[px] * (Gc - Gr[px]) - __fdividef(Tp[px], 1.0f - al) * Gbr[px];
-                const float kc = kA[px] * al * w;
-                acc[0] += kc * G[px][0];
-                acc[1] += kc * G[px][1];
-                acc[2] += kc * G[px][2];
-                acc[3] += kA[px] * al * (Gc - Gr[px]);
-                if (araw < 0.99f && io > 0.0f) {
-                    acc[4] += gal * (al * io);
-                    const float gq = -0.5f * al * gal;
-                    acc[5] += -2.0f * gq * (cA * dx + cB * dy);
-                    acc[6] += -2.0f * gq * (cB * dx + cC * dy);
-                    acc[7] += gq * dx * dx;
-                    acc[8] += 2.0f * gq * dx * dy;
-                    acc[9] += gq * dy * dy;
+                sc0 = fmaf(al, kG[px][0], sc0);
+                sc1 = fmaf(al, kG[px][1], sc1);
+                sc2 = fmaf(al, kG[px][2], sc2);
+                const float u = fmaf(kG[px][0], cr, fmaf(kG[px][1], cg, fmaf(kG[px][2], cb, -kGr[px])));
+                sw = fmaf(al, u, sw);
+                if (araw < 0.99f) {
+                    // 1 - al > 0.01: the fast reciprocal division is accurate to a few ulp
+                    const float sa = al * fmaf(w, u, -__fdividef(TGb[px], 1.0f - al));
+                    s0 += sa;
+                    s1 = fmaf(sa, dx, s1);
+                    s2 = fmaf(sa * dx, dx, s2);
                 }
+            }
+            float acc[10];
+            acc[0] = w * sc0;
+            acc[1] = w * sc1;
+            acc[2] = w * sc2;
+            acc[3] = sw;
+            if (io > 0.0f) {
+                // dL/dq = -s / 2 per pixel; q = A dx^2 + 2 B dx dy + C dy^2 gives
+                // dq/dm = -2 (A dx + B dy, B dx + C dy) and dq/d(A, B, C) =
+                // (dx^2, 2 dx dy, dy^2)
+                acc[4] = s0 * io;
+                acc[5] = fmaf(cA, s1, cB * dy * s0);
+                acc[6] = fmaf(cB, s1, cC * dy * s0);
+                acc[7] = -0.5f * s2;
+                acc[8] = -dy * s1;
+                acc[9] = -0.5f * dy * dy * s0;
+            } else {
+                acc[4] = acc[5] = acc[6] = acc[7] = acc[8] = acc[9] = 0.f;
             }
 #pragma unroll
             for (int e = 0; e < 10; ++e) red[warp][(k - k0) * 10 + e][lane] = acc[e];
