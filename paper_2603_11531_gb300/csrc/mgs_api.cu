@@ -95,7 +95,7 @@ struct mgs_workspace_s {
     uint32_t *tile_offsets = nullptr;
     uint32_t *tile_order = nullptr;
     uint32_t *gids = nullptr;
-    uint32_t *bases = nullptr;   // [binning CTAs][tiles] block bases
+    uint32_t *bases = nullptr;   // binning scratch: [binning CTAs][tiles] block bases, group scan
     int64_t bases_cap = 0;
     float *img = nullptr;
     float *bwd_g = nullptr;        // backward: per-Gaussian raster gradients
@@ -151,7 +151,7 @@ mgs_status ws_ensure(mgs_workspace_s *w, int64_t n, int64_t tiles, uint64_t pair
         if ((e = dev_alloc(&w->gids, (size_t)pairs)) != cudaSuccess) return cuda_fail(e, "workspace");
         w->pair_cap = pairs;
     }
-    const int64_t nb = (int64_t)bin_ctas(n, w->ctx->sm_count) * tiles;
+    const int64_t nb = bin_scratch_words(n, tiles, w->ctx->sm_count);
     if (nb > w->bases_cap) {
         dev_free(w->bases);
         w->bases_cap = 0;

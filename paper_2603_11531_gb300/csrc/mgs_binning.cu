@@ -4,17 +4,22 @@
 // (Sec. 2, Eq. 1 discussion; Sec. 3.1).  The lists built here are keyed by
 // tile only -- a counting sort by tile:
 //
-//   1. k_bin_count: CTA c owns a contiguous range of Gaussians and counts its
-//      (tile, Gaussian) pairs into a shared-memory histogram over the tiles;
-//      one global atomicAdd per (CTA, tile) reserves the CTA's block inside
-//      the tile and returns its base.
+//   0. k_group_pairs, k_bin_plan: rectangle pair counts of every group of 32
+//      consecutive Gaussians and the exclusive scan of the group costs (pairs
+//      plus a fixed visit charge).  Every warp of the binning grid takes an
+//      equal contiguous share of that cost numbering, so neither a warp nor
+//      an SM waits on a few Gaussians that cover many tiles, nor on a long
+//      stretch of Gaussians that cover almost none.
+//   1. k_bin_count: each CTA counts the pairs of its warps' shares into a
+//      shared-memory histogram over the tiles; one global atomicAdd per (CTA,
+//      tile) reserves the CTA's block inside the tile and returns its base.
 //   2. k_scan: exclusive scan of the per-tile totals -> tile offsets.
-//   3. k_bin_scatter: the same CTA re-expands its pairs and places each one at
-//      offset[tile] + base[c][tile] + (shared-memory rank).
+//   3. k_bin_scatter: the same CTA re-expands the same pairs and places each
+//      one at offset[tile] + base[c][tile] + (shared-memory rank).
 //
-// Pairs are expanded warp-cooperatively: a warp's 32 Gaussians are flattened
-// into one pair index space (prefix sum of rectangle areas) so a Gaussian
-// covering thousands of tiles does not serialise one lane.  A pair is listed
+// Pairs are expanded warp-cooperatively: a group's 32 Gaussians are
+// flattened into one pair index space (prefix sum of rectangle areas) so a
+// Gaussian covering thousands of tiles does not serialise one lane.  A pair is listed
 // only if the FP32 tile test (tile_may_hit) allows an included pixel in the
 // tile; its rectangle alone (the 3-sigma bounding square) would list many
 // tiles a thin ellipse never reaches.  Order within a
@@ -35,6 +40,8 @@ __device__ __forceinline__ void rect_of(const uint2 r, int &x0, int &y0, int &w,
     w = (int)(r.x >> 16) - x0;
     h = (int)(r.y >> 16) - y0;
 }
+// Number of (tile, Gaussian) pairs of a rectangle.
+__device__ __forceinline__ int rect_pairs(int w, int h) { return w > 0 && h > 0 ? w * h : 0; }
 
 // FP32-contract tile test: may Gaussian (m, l) include a pixel centre of tile
 // (tx, ty)?  Slab bounds at the tile centre with half extent 7.5 and a 2^-18
@@ -58,13 +65,14 @@ __device__ __forceinline__ bool tile_may_hit(float mx, float my, float l11, floa
     return __fsub_rn(e1c, h1) <= __fadd_rn(3.0f, m1) && __fsub_rn(e2c, h2) <= __fadd_rn(3.0f, m2);
 }
 
-// Calls f(tile, gid) for every (tile, Gaussian) pair of Gaussians
-// [g0, g0 + 32) (one per lane) whose tile passes tile_may_hit, spreading the
-// pairs of the rectangles over the warp's lanes.
+// Calls f(tile, gid) for the pairs [pa, pb) of the flattened pair numbering
+// of Gaussians [g0, g0 + 32) (one per lane; rectangle after rectangle, row
+// major inside each) whose tile passes tile_may_hit, 32 pairs at a time
+// over the warp's lanes.
 template <class F>
 __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
                                            const ProjRec *__restrict__ rec, int64_t n, int64_t g0,
-                                           int tiles_x, F &&f) {
+                                           int tiles_x, int pa, int pb, F &&f) {
     const int lane = threadIdx.x & 31;
     const int64_t i = g0 + lane;
     int x0 = 0, y0 = 0, w = 0, h = 0;
@@ -77,7 +85,7 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
             gl22 = rec[i].b.x;
         }
     }
-    const int c = w * h;
+    const int c = rect_pairs(w, h);
     const float winv = w > 0 ? 1.0f / (float)w : 0.0f;
     int incl = c;
 #pragma unroll
@@ -86,9 +94,9 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
         if (lane >= o) incl += y;
     }
     const int excl = incl - c;
-    const int P = __shfl_sync(0xffffffffu, incl, 31);
-    for (int pb = 0; pb < P; pb += 32) {
-        const int p = pb + lane;
+    const int P = min(__shfl_sync(0xffffffffu, incl, 31), pb);
+    for (int base = pa; base < P; base += 32) {
+        const int p = base + lane;
         // owner: the largest lane whose exclusive prefix is <= p
         int lo = 0;
 #pragma unroll
@@ -119,31 +127,140 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
     }
 }
 
-__device__ __forceinline__ void cta_range(int64_t n, int64_t &begin, int64_t &end) {
-    const int64_t per = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
-    begin = per * blockIdx.x;
-    end = begin + per < n ? begin + per : n;
+// Cost of a group in the work plan: its rectangle pairs plus a fixed charge
+// for visiting it (loading and scanning 32 rectangles), so that shares over
+// sparse stretches of the scene (many Gaussians, few pairs) stay short.
+constexpr int kGroupCost = 64;
+
+// Largest group g with cexcl[g] <= c (c < cexcl[groups]).
+__device__ __forceinline__ int64_t find_group(const unsigned long long *__restrict__ cexcl,
+                                              int64_t groups, unsigned long long c) {
+    int64_t lo = 0, hi = groups - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (cexcl[mid] <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
-__global__ void __launch_bounds__(kBinThreads) k_bin_count(const uint2 *__restrict__ rect,
+// Calls f(tile, gid) for the listed pairs of this warp's share of the work
+// plan: group g occupies costs [cexcl[g], cexcl[g + 1]), its visit charge
+// first and then one unit per rectangle pair in the group's pair numbering;
+// warp w of W takes costs [C w / W, C (w + 1) / W) of the total C.
+template <class F>
+__device__ __forceinline__ void warp_share_pairs(const uint2 *__restrict__ rect,
+                                                 const ProjRec *__restrict__ rec, int64_t n,
+                                                 const unsigned long long *__restrict__ cexcl,
+                                                 int64_t groups, int tiles_x, F &&f) {
+    if (groups == 0) return;
+    const unsigned long long C = cexcl[groups];
+    const unsigned long long W = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long w = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const unsigned long long c0 = C * w / W, c1 = C * (w + 1) / W;
+    if (c0 >= c1) return;
+    int64_t g = find_group(cexcl, groups, c0);
+    unsigned long long e0 = cexcl[g];
+    for (;;) {
+        const unsigned long long e1 = cexcl[g + 1];
+        const long long np = (long long)(e1 - e0) - kGroupCost;    // pairs of group g
+        const long long pa = max(0ll, (long long)(c0 > e0 ? c0 - e0 : 0ull) - kGroupCost);
+        const long long pb = min(np, (long long)(c1 - e0) - kGroupCost);
+        if (pa < pb) warp_pairs(rect, rec, n, g * 32, tiles_x, (int)pa, (int)pb, f);
+        if (c1 <= e1 || g + 1 >= groups) break;
+        ++g;
+        e0 = e1;
+    }
+}
+
+// Rectangle pair count of every group of 32 consecutive Gaussians (one warp
+// per group).
+__global__ void __launch_bounds__(kBinThreads) k_group_pairs(const uint2 *__restrict__ rect,
+                                                             int64_t n, uint32_t *__restrict__ grp) {
+    const int64_t g = ((int64_t)blockIdx.x * kBinThreads + threadIdx.x) >> 5;
+    const int64_t i = g * 32 + (threadIdx.x & 31);
+    uint32_t c = 0;
+    if (i < n) {
+        int x0, y0, w, h;
+        rect_of(rect[i], x0, y0, w, h);
+        c = (uint32_t)rect_pairs(w, h);
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && g * 32 < n) grp[g] = c;
+}
+
+// Exclusive scan of the group costs (pairs + kGroupCost) into
+// cexcl[0..groups] (64-bit), by one block, kPlanSeg groups at a time staged
+// in shared memory so that global loads and stores stay coalesced.
+constexpr int kPlanSeg = 16384;   // 64-bit costs per pass
+// Shared-memory slot of entry i: one pad word every 16 entries, so that
+// threads scanning runs of 16 consecutive entries hit different banks.
+__device__ __forceinline__ int plan_slot(int i) { return i + (i >> 4); }
+constexpr int kPlanSlots = kPlanSeg + kPlanSeg / 16;
+__global__ void __launch_bounds__(kScanThreads) k_bin_plan(const uint32_t *__restrict__ grp,
+                                                           int64_t groups,
+                                                           unsigned long long *__restrict__ cexcl) {
+    extern __shared__ unsigned long long seg[];
+    __shared__ unsigned long long warp_sums[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long carry = 0;   // identical in every thread
+    for (int64_t s0 = 0; s0 < groups; s0 += kPlanSeg) {
+        const int m = (int)(groups - s0 < kPlanSeg ? groups - s0 : kPlanSeg);
+        for (int i = tid; i < m; i += kScanThreads)
+            seg[plan_slot(i)] = (unsigned long long)grp[s0 + i] + kGroupCost;
+        __syncthreads();
+        const int per = (m + kScanThreads - 1) / kScanThreads;
+        const int lo = min(tid * per, m), hi = min(lo + per, m);
+        unsigned long long local = 0;
+        for (int i = lo; i < hi; ++i) local += seg[plan_slot(i)];
+        unsigned long long incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long t = warp_sums[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_sums[lane] = t;
+        }
+        __syncthreads();
+        unsigned long long run = carry + (incl - local) + (warp > 0 ? warp_sums[warp - 1] : 0ull);
+        for (int i = lo; i < hi; ++i) {
+            const unsigned long long v = seg[plan_slot(i)];
+            seg[plan_slot(i)] = run;
+            run += v;
+        }
+        carry += warp_sums[kScanThreads / 32 - 1];
+        __syncthreads();
+        for (int i = tid; i < m; i += kScanThreads) cexcl[s0 + i] = seg[plan_slot(i)];
+        __syncthreads();
+    }
+    if (tid == 0) cexcl[groups] = carry;
+}
+
+__global__ void __launch_bounds__(kBinThreads, 1) k_bin_count(const uint2 *__restrict__ rect,
                                                            const ProjRec *__restrict__ rec,
                                                            int64_t n, int tiles_x, int T,
+                                                           const unsigned long long *__restrict__ excl,
+                                                           int64_t groups,
                                                            uint32_t *__restrict__ tile_count,
                                                            uint32_t *__restrict__ bases) {
     extern __shared__ uint32_t cnt_s[];
-    int64_t begin, end;
-    cta_range(n, begin, end);
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int band0 = 0; band0 < T; band0 += kBand) {
         const int bn = min(kBand, T - band0);
         for (int t = threadIdx.x; t < bn; t += blockDim.x) cnt_s[t] = 0u;
         __syncthreads();
-        for (int64_t g0 = begin + 32 * warp; g0 < end; g0 += 32 * nwarps) {
-            warp_pairs(rect, rec, end, g0, tiles_x, [&](int tile, uint32_t) {
-                const int t = tile - band0;
-                if ((unsigned)t < (unsigned)bn) atomicAdd(&cnt_s[t], 1u);
-            });
-        }
+        warp_share_pairs(rect, rec, n, excl, groups, tiles_x, [&](int tile, uint32_t) {
+            const int t = tile - band0;
+            if ((unsigned)t < (unsigned)bn) atomicAdd(&cnt_s[t], 1u);
+        });
         __syncthreads();
         for (int t = threadIdx.x; t < bn; t += blockDim.x) {
             const uint32_t v = cnt_s[t];
@@ -172,39 +289,36 @@ __device__ __forceinline__ uint4 weights_f16(const ProjRec &r, float scale) {
     return u;
 }
 
-__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(
+__global__ void __launch_bounds__(kBinThreads, 1) k_bin_scatter(
     const uint2 *__restrict__ rect, int64_t n, int tiles_x, int T,
+    const unsigned long long *__restrict__ excl, int64_t groups,
     const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ bases,
     uint32_t *__restrict__ gids, uint64_t capacity, const DevStatus *__restrict__ status,
     const ProjRec *__restrict__ rec, uint4 *__restrict__ wt16) {
     extern __shared__ uint32_t cur_s[];
     if (status->last_pairs > capacity) return;  // overflow: lists are not built
-    int64_t begin, end;
-    cta_range(n, begin, end);
     if (wt16) {   // tensor-core rasteriser: FP16 weights of the visible Gaussians
         const int we = (int)((status->wmax_frame_bits >> 23) & 0xFFu) - 127;
         const float scale = we >= 14 ? __int_as_float((127 + 14 - we) << 23) : 1.0f;
-        for (int64_t g = begin + threadIdx.x; g < end; g += blockDim.x) {
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+             g += (int64_t)gridDim.x * blockDim.x) {
             const uint2 r = rect[g];
             if (r.x | r.y) wt16[g] = weights_f16(rec[g], scale);
         }
     }
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int band0 = 0; band0 < T; band0 += kBand) {
         const int bn = min(kBand, T - band0);
         // entries of tiles this CTA has no pairs in are never read
         for (int t = threadIdx.x; t < bn; t += blockDim.x)
             cur_s[t] = offsets[band0 + t] + bases[(int64_t)blockIdx.x * T + band0 + t];
         __syncthreads();
-        for (int64_t g0 = begin + 32 * warp; g0 < end; g0 += 32 * nwarps) {
-            warp_pairs(rect, rec, end, g0, tiles_x, [&](int tile, uint32_t gid) {
-                const int t = tile - band0;
-                if ((unsigned)t < (unsigned)bn) {
-                    const uint32_t slot = atomicAdd(&cur_s[t], 1u);
-                    if (slot < capacity) gids[slot] = gid;
-                }
-            });
-        }
+        warp_share_pairs(rect, rec, n, excl, groups, tiles_x, [&](int tile, uint32_t gid) {
+            const int t = tile - band0;
+            if ((unsigned)t < (unsigned)bn) {
+                const uint32_t slot = atomicAdd(&cur_s[t], 1u);
+                if (slot < capacity) gids[slot] = gid;
+            }
+        });
         __syncthreads();
     }
 }
@@ -302,17 +416,28 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_order(const uint32_t *__r
 
 }  // namespace
 
+// One 1024-thread CTA per SM at most: the work plan balances the warps, so a
+// second resident CTA would only add per-CTA tile bases.
 int bin_ctas(int64_t n, int sm_count) {
     int64_t c = (n + kBinThreads - 1) / kBinThreads;
-    const int64_t cap = 2 * (int64_t)sm_count;
+    const int64_t cap = (int64_t)sm_count;
     if (c > cap) c = cap;
     return c < 1 ? 1 : (int)c;
 }
 
-cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases,
+int64_t bin_scratch_words(int64_t n, int64_t T, int sm_count) {
+    return bin_scratch_words_for(bin_ctas(n, sm_count), T, n);
+}
+
+cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch,
                            cudaStream_t stream) {
     const int T = a.cam.tiles_x * a.cam.tiles_y;
     const int C = bin_ctas(a.n, sm_count);
+    const int64_t groups = (a.n + 31) / 32;
+    uint32_t *bases = scratch;
+    unsigned long long *excl =
+        reinterpret_cast<unsigned long long *>(scratch + ((int64_t)C * T + 1) / 2 * 2);
+    uint32_t *grp = reinterpret_cast<uint32_t *>(excl + groups + 1);
     const size_t smem = (size_t)(T < kBand ? T : kBand) * sizeof(uint32_t);
     cudaError_t e = cudaMemsetAsync(a.tile_count, 0, (size_t)T * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
@@ -323,17 +448,27 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases,
         if ((e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(kBand * sizeof(uint32_t)))) != cudaSuccess)
             return e;
-        k_bin_count<<<C, kBinThreads, smem, stream>>>(a.rect, a.rec, a.n, a.cam.tiles_x, T,
-                                                      a.tile_count, bases);
+        k_group_pairs<<<(int)((groups * 32 + kBinThreads - 1) / kBinThreads), kBinThreads, 0,
+                        stream>>>(a.rect, a.n, grp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int plan_n = (int)(groups < kPlanSeg ? groups : kPlanSeg);
+        const size_t plan_smem = (size_t)(plan_n + plan_n / 16) * sizeof(unsigned long long);
+        if ((e = cudaFuncSetAttribute(k_bin_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kPlanSlots * sizeof(unsigned long long)))) != cudaSuccess)
+            return e;
+        k_bin_plan<<<1, kScanThreads, plan_smem, stream>>>(grp, groups, excl);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_bin_count<<<C, kBinThreads, smem, stream>>>(a.rect, a.rec, a.n, a.cam.tiles_x, T, excl,
+                                                      groups, a.tile_count, bases);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_scan<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, T, a.capacity, a.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_tile_order<<<1, kScanThreads, 0, stream>>>(a.tile_count, T, a.tile_order, a.status);
     if ((e = cudaGetLastError()) != cudaSuccess || a.n == 0) return e;
-    k_bin_scatter<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, a.tile_offsets,
-                                                    bases, a.gids, a.capacity, a.status, a.rec,
-                                                    tc_raster(a) ? a.wt16 : nullptr);
+    k_bin_scatter<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, excl, groups,
+                                                    a.tile_offsets, bases, a.gids, a.capacity,
+                                                    a.status, a.rec, tc_raster(a) ? a.wt16 : nullptr);
     return cudaGetLastError();
 }
 

@@ -188,9 +188,15 @@ cudaError_t launch_sorted(const RenderArgs &a, const SortedScratch &s, cudaStrea
 
 // Launchers (each enqueues its kernels on `stream`).
 cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t stream);
-// Per-tile counts, scan and scatter.  `bases` has bin_ctas(...) * T entries.
-cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *bases, cudaStream_t stream);
+// Per-tile counts, scan and scatter.  `scratch` has bin_scratch_words(n, T,
+// sm_count) 32-bit words: the per-CTA tile bases, then the pair counts of the
+// 32-Gaussian groups and their exclusive scan.
+cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch, cudaStream_t stream);
 int bin_ctas(int64_t n, int sm_count);
+__host__ __device__ constexpr int64_t bin_scratch_words_for(int64_t ctas, int64_t T, int64_t n) {
+    return (ctas * T + 1) / 2 * 2 + 2 * ((n + 31) / 32 + 1) + (n + 31) / 32;
+}
+int64_t bin_scratch_words(int64_t n, int64_t T, int sm_count);
 // Backward pass (mgs_backward.cu): gG [n][grad_record_size()] scratch,
 // partials [pre_bwd_blocks()][mlp_grad_size()] scratch, d_attrs [n][24],
 // d_mlp [mlp_grad_size()] (nullable).

@@ -116,7 +116,7 @@ uint64_t cache_key(mgs_scene s, int w, int h) {
 int64_t estimate_bytes(int64_t n, int w, int h, uint64_t pairs, int sm_count) {
     const int64_t T = (int64_t)((w + kTile - 1) / kTile) * ((h + kTile - 1) / kTile);
     return n * (int64_t)(sizeof(ProjRec) + sizeof(uint2)) + (T + 1) * 12 +
-           (int64_t)bin_ctas(n, sm_count) * T * 4 + (int64_t)pairs * 4 + 4096;
+           bin_scratch_words(n, T, sm_count) * 4 + (int64_t)pairs * 4 + 4096;
 }
 
 // Runs the request's preprocessing and binning on the slot's stream, as a

@@ -35,7 +35,8 @@ constexpr size_t kCountOff = kRectOff + align256(kMaxGaussians * sizeof(uint2));
 constexpr size_t kOffsetsOff = kCountOff + align256((kMaxTiles + 1) * sizeof(uint32_t));
 constexpr size_t kOrderOff = kOffsetsOff + align256((kMaxTiles + 1) * sizeof(uint32_t));
 constexpr size_t kBasesOff = kOrderOff + align256((kMaxTiles + 1) * sizeof(uint32_t));
-constexpr size_t kGidsOff = kBasesOff + align256((size_t)kMaxBinCtas * kMaxTiles * sizeof(uint32_t));
+constexpr size_t kGidsOff =
+    kBasesOff + align256((size_t)bin_scratch_words_for(kMaxBinCtas, kMaxTiles, kMaxGaussians) * sizeof(uint32_t));
 constexpr size_t kWt16Off = kGidsOff + align256(kMaxPairs * sizeof(uint32_t));
 constexpr size_t kStatusOff = kWt16Off + align256(kMaxGaussians * sizeof(uint4));
 constexpr size_t kScratchBytes = kStatusOff + align256(sizeof(DevStatus));  // ~29 MiB
