@@ -269,3 +269,33 @@ def test_all_poses_reduced_resolution(R):
     finally:
         R.unload_scene(h)
     assert math.isfinite(err)
+
+
+def test_binning_work_plan_cases(R):
+    """Tile lists and pixels for scenes that stress the binning work plan
+    (equal shares of the 32-Gaussian groups' pair counts plus a per-group
+    visit charge): long runs of groups without pairs between visible ones,
+    a ragged last group, fewer plan units than warps, and one Gaussian that
+    covers every tile among many small ones."""
+    cam = synth.look_at((0, 0, -3), (0, 0, 0), 200, 136, 60.0)
+    # 20,011 Gaussians: index ranges [3000, 9000) and [12000, 19000) moved
+    # behind the camera, so thousands of consecutive groups have no pairs
+    sc = synth.uniform_scene(20011, seed=41, precision="fp32")
+    a = sc.attrs.copy()
+    a[3000:9000, 2] = -20.0
+    a[12000:19000, 2] = -20.0
+    out, ref = _render_both(R, synth.Scene(a), cam, bg=(0.1, 0.2, 0.3))
+    np.testing.assert_array_equal(out["count"], ref["count"])
+    assert np.abs(out["rgb"] - ref["rgb"]).max() <= TOL_FP32
+    # 37 Gaussians (two groups, the second ragged): far fewer plan units than warps
+    few = synth.uniform_scene(37, seed=42, precision="fp32")
+    out, ref = _render_both(R, few, cam)
+    np.testing.assert_array_equal(out["count"], ref["count"])
+    assert np.abs(out["rgb"] - ref["rgb"]).max() <= TOL_FP32
+    # one Gaussian at the centre, scaled to cover the whole image, among 5,000
+    big = synth.uniform_scene(5000, seed=43, precision="fp32").attrs.copy()
+    big[2500, 0:3] = 0.0
+    big[2500, 3:6] = 3.0
+    out, ref = _render_both(R, synth.Scene(big), cam)
+    np.testing.assert_array_equal(out["count"], ref["count"])
+    assert np.abs(out["rgb"] - ref["rgb"]).max() <= TOL_FP32
