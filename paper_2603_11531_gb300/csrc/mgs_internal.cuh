@@ -44,7 +44,8 @@ struct DevMLP {
 
 // Shared-memory layout (byte offsets) of the wide (three hidden layer)
 // tcgen05 MLP for one 128-row tile: BF16 operands in canonical K-major
-// layout (x, activations a0/a1, weights w1..w3), the FP32 head and biases.
+// layout (x, activations a0/a1, weights w1..w3), the FP32 head ([h3][8],
+// input-major, outputs 5..7 zero) and biases.
 struct WideLayout {
     uint32_t x, a0, a1, w1, w2, w3, head, b1, b2, b3, b4, mbar, tmem, total;
 };
@@ -63,7 +64,7 @@ __host__ __device__ inline WideLayout wide_layout(int h1, int h2, int h3) {
     L.w1 = take((uint32_t)h1 * 32u * 2u, 128u);
     L.w2 = take((uint32_t)h2 * (uint32_t)h1 * 2u, 128u);
     L.w3 = take((uint32_t)h3 * (uint32_t)h2 * 2u, 128u);
-    L.head = take(5u * (uint32_t)h3 * 4u, 16u);
+    L.head = take(8u * (uint32_t)h3 * 4u, 16u);
     L.b1 = take((uint32_t)h1 * 4u, 16u);
     L.b2 = take((uint32_t)h2 * 4u, 16u);
     L.b3 = take((uint32_t)h3 * 4u, 16u);

@@ -23,6 +23,7 @@
 #include "mgs_internal.cuh"
 
 namespace mgs {
+static_assert(kMlpOut == 5, "the CUDA-core heads below unroll five outputs");
 namespace tc {
 
 constexpr int kRows = 128;          // rows per MMA tile
@@ -126,7 +127,7 @@ struct Smem {
     alignas(128) __nv_bfloat16 h1[kTiles][kRows * kMlpHidden];  // A of layer 2, K = 64
     alignas(128) __nv_bfloat16 w1[kMlpHidden * kMlpK1];         // B, N = 64, K = 32
     alignas(128) __nv_bfloat16 w2[kMlpHidden * kMlpHidden];     // B, N = 64, K = 64
-    float w3[kMlpOut][kMlpHidden];                               // head (BF16 values)
+    alignas(16) float w3[kMlpHidden][8];                         // head (BF16 values), [in][out]
     float b1[kMlpHidden], b2[kMlpHidden], b3[kMlpOut];
     alignas(8) unsigned long long mbar;
     uint32_t tmem_base;
@@ -138,6 +139,18 @@ __device__ __forceinline__ void store_bf16x2(__nv_bfloat16 *base, uint32_t off, 
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<unsigned char *>(base) + off) = h;
 }
+
+// BF16(max(lo, 0)) | BF16(max(hi, 0)) << 16, round to nearest even, in one
+// conversion.  A NaN stays NaN (max(NaN, 0) would give 0): rows that can
+// carry NaN features (zero quaternion, mean at the camera centre) are culled
+// before their MLP outputs are used.
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
 
 // Loads the packed weights into canonical layout, initialises the mbarrier
 // and allocates TMEM.  All threads of the CTA must call it.
@@ -152,8 +165,10 @@ __device__ __forceinline__ void setup(Smem &sm, const DevMLP &mlp) {
         *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(sm.w2) +
                                            core_off(n, k, kMlpHidden)) = mlp.w2[e];
     }
-    for (int e = threadIdx.x; e < kMlpOut * kMlpHidden; e += blockDim.x)
-        sm.w3[e / kMlpHidden][e % kMlpHidden] = __bfloat162float(mlp.w3[e]);
+    for (int e = threadIdx.x; e < kMlpHidden * 8; e += blockDim.x) {
+        const int c = e >> 3, k = e & 7;
+        sm.w3[c][k] = k < kMlpOut ? __bfloat162float(mlp.w3[k * kMlpHidden + c]) : 0.0f;
+    }
     for (int e = threadIdx.x; e < kMlpHidden; e += blockDim.x) {
         sm.b1[e] = mlp.b1[e];
         sm.b2[e] = mlp.b2[e];
@@ -239,9 +254,15 @@ __device__ __forceinline__ bool mlp_cta(Smem &sm, uint32_t &phase, float (&out)[
         float v[16];
         ld16(col0 + (uint32_t)c, v);
 #pragma unroll
-        for (int i = 0; i < 16; i += 2)
-            store_bf16x2(sm.h1[tile], core_off(row, c + i, kMlpHidden),
-                         fmaxf(v[i] + sm.b1[c + i], 0.0f), fmaxf(v[i + 1] + sm.b1[c + i + 1], 0.0f));
+        for (int h = 0; h < 16; h += 8) {
+            uint4 u;
+            u.x = relu_bf16x2(v[h] + sm.b1[c + h], v[h + 1] + sm.b1[c + h + 1]);
+            u.y = relu_bf16x2(v[h + 2] + sm.b1[c + h + 2], v[h + 3] + sm.b1[c + h + 3]);
+            u.z = relu_bf16x2(v[h + 4] + sm.b1[c + h + 4], v[h + 5] + sm.b1[c + h + 5]);
+            u.w = relu_bf16x2(v[h + 6] + sm.b1[c + h + 6], v[h + 7] + sm.b1[c + h + 7]);
+            *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(sm.h1[tile]) +
+                                       core_off(row, c + h, kMlpHidden)) = u;
+        }
     }
     fence_async_smem();
     fence_before();
@@ -256,11 +277,20 @@ __device__ __forceinline__ bool mlp_cta(Smem &sm, uint32_t &phase, float (&out)[
         float v[16];
         ld16(col0 + (uint32_t)c, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < 16; i += 2) {
             // h2 = BF16(ReLU(.)), the same rounding the head MMA would see
-            const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(v[i] + sm.b2[c + i], 0.0f)));
+            const uint32_t hp = relu_bf16x2(v[i] + sm.b2[c + i], v[i + 1] + sm.b2[c + i + 1]);
 #pragma unroll
-            for (int k = 0; k < kMlpOut; ++k) acc[k] = fmaf(sm.w3[k][c + i], h, acc[k]);
+            for (int j = 0; j < 2; ++j) {
+                const float h = j ? bf16_hi(hp) : bf16_lo(hp);
+                const float4 w = *reinterpret_cast<const float4 *>(&sm.w3[c + i + j][0]);
+                const float w4 = sm.w3[c + i + j][4];
+                acc[0] = fmaf(w.x, h, acc[0]);
+                acc[1] = fmaf(w.y, h, acc[1]);
+                acc[2] = fmaf(w.z, h, acc[2]);
+                acc[3] = fmaf(w.w, h, acc[3]);
+                acc[4] = fmaf(w4, h, acc[4]);
+            }
         }
     }
 #pragma unroll
@@ -297,8 +327,11 @@ __device__ __forceinline__ void setup(unsigned char *base, const WideLayout &L, 
         put_bf16(base, L.w2, e / h1, e % h1, h1, mlp.w2[e]);
     for (int e = threadIdx.x; e < h3 * h2; e += blockDim.x)
         put_bf16(base, L.w3, e / h2, e % h2, h2, mlp.w3[e]);
-    float *head = reinterpret_cast<float *>(base + L.head);
-    for (int e = threadIdx.x; e < kMlpOut * h3; e += blockDim.x) head[e] = __bfloat162float(mlp.w4[e]);
+    float *head = reinterpret_cast<float *>(base + L.head);   // [h3][8]: input-major
+    for (int e = threadIdx.x; e < h3 * 8; e += blockDim.x) {
+        const int c = e >> 3, k = e & 7;
+        head[e] = k < kMlpOut ? __bfloat162float(mlp.w4[k * h3 + c]) : 0.0f;
+    }
     float *b1 = reinterpret_cast<float *>(base + L.b1);
     float *b2 = reinterpret_cast<float *>(base + L.b2);
     float *b3 = reinterpret_cast<float *>(base + L.b3);
@@ -385,12 +418,9 @@ __device__ __forceinline__ void relu_to_bf16(unsigned char *base, const WideLayo
                 uint4 u;
                 uint32_t *w = &u.x;
 #pragma unroll
-                for (int i = 0; i < 8; i += 2) {
-                    const __nv_bfloat162 p =
-                        __floats2bfloat162_rn(fmaxf(__uint_as_float(r[q][h + i]) + b[c + i], 0.0f),
-                                              fmaxf(__uint_as_float(r[q][h + i + 1]) + b[c + i + 1], 0.0f));
-                    w[i / 2] = *reinterpret_cast<const uint32_t *>(&p);
-                }
+                for (int i = 0; i < 8; i += 2)
+                    w[i / 2] = tc::relu_bf16x2(__uint_as_float(r[q][h + i]) + b[c + i],
+                                               __uint_as_float(r[q][h + i + 1]) + b[c + i + 1]);
                 *reinterpret_cast<uint4 *>(base + out_off + tc::core_off(row, c, N)) = u;
             }
         }
@@ -445,12 +475,21 @@ __device__ __forceinline__ bool mlp_cta(unsigned char *base, const WideLayout &L
         for (int q = 0; q < 4; ++q) {
             if (c0 + 16 * q >= h3) break;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < 16; i += 2) {
                 const int c = c0 + 16 * q + i;
-                const float h =
-                    __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(r[q][i]) + b3[c], 0.0f)));
+                const uint32_t hp = tc::relu_bf16x2(__uint_as_float(r[q][i]) + b3[c],
+                                                    __uint_as_float(r[q][i + 1]) + b3[c + 1]);
 #pragma unroll
-                for (int k = 0; k < kMlpOut; ++k) acc[k] = fmaf(head[k * h3 + c], h, acc[k]);
+                for (int j = 0; j < 2; ++j) {
+                    const float h = j ? tc::bf16_hi(hp) : tc::bf16_lo(hp);
+                    const float4 w = *reinterpret_cast<const float4 *>(head + (c + j) * 8);
+                    const float w4 = head[(c + j) * 8 + 4];
+                    acc[0] = fmaf(w.x, h, acc[0]);
+                    acc[1] = fmaf(w.y, h, acc[1]);
+                    acc[2] = fmaf(w.z, h, acc[2]);
+                    acc[3] = fmaf(w.w, h, acc[3]);
+                    acc[4] = fmaf(w4, h, acc[4]);
+                }
             }
         }
     }
