@@ -43,11 +43,12 @@ struct DevMLP {
 };
 
 // Shared-memory layout (byte offsets) of the wide (three hidden layer)
-// tcgen05 MLP for one 128-row tile: BF16 operands in canonical K-major
-// layout (x, activations a0/a1, weights w1..w3), the FP32 head ([h3][8],
-// input-major, outputs 5..7 zero) and biases.
+// tcgen05 MLP, two 128-row tiles per step: BF16 operands in canonical K-major
+// layout (features x of both tiles, activations a0/a1 of the current tile,
+// weights w1..w3), the FP32 head ([h3][8], input-major, outputs 5..7 zero),
+// biases, and the head partial sums exchanged between the two warp halves.
 struct WideLayout {
-    uint32_t x, a0, a1, w1, w2, w3, head, b1, b2, b3, b4, mbar, tmem, total;
+    uint32_t x, a0, a1, w1, w2, w3, head, b1, b2, b3, b4, red, mbar, tmem, total;
 };
 __host__ __device__ inline WideLayout wide_layout(int h1, int h2, int h3) {
     WideLayout L{};
@@ -58,7 +59,7 @@ __host__ __device__ inline WideLayout wide_layout(int h1, int h2, int h3) {
         o += bytes;
         return r;
     };
-    L.x = take(128u * 32u * 2u, 128u);
+    L.x = take(2u * 128u * 32u * 2u, 128u);   // features of the step's two tiles
     L.a0 = take(128u * (uint32_t)h1 * 2u, 128u);
     L.a1 = take(128u * (uint32_t)h2 * 2u, 128u);
     L.w1 = take((uint32_t)h1 * 32u * 2u, 128u);
@@ -69,6 +70,7 @@ __host__ __device__ inline WideLayout wide_layout(int h1, int h2, int h3) {
     L.b2 = take((uint32_t)h2 * 4u, 16u);
     L.b3 = take((uint32_t)h3 * 4u, 16u);
     L.b4 = take(8u * 4u, 16u);
+    L.red = take(128u * 8u * 4u, 16u);        // head partial sums of one warp half
     L.mbar = take(8u, 8u);
     L.tmem = take(4u, 4u);
     L.total = o;

@@ -304,15 +304,30 @@ __device__ __forceinline__ bool mlp_cta(Smem &sm, uint32_t &phase, float (&out)[
 
 // ---------------------------------------------------------------------------
 // The paper-width MLP_f (App. C: three hidden layers, e.g. 256, 128, 64):
-// one CTA of 128 threads evaluates 128 Gaussians per step; layer l is one
-// M = 128, N = h_l tcgen05 MMA chain (K = 16 per instruction) whose FP32
-// accumulator occupies TMEM columns 0 .. h_l - 1 (256 columns allocated);
-// thread t reads row t, adds the bias, applies ReLU, rounds to BF16 and
-// writes the next layer's A operand; the 5-wide head runs on CUDA cores.
+// one CTA of 256 threads evaluates 256 Gaussians per step as two M = 128
+// tiles, one after the other; layer l of a tile is one M = 128, N = h_l
+// tcgen05 MMA chain (K = 16 per instruction) whose FP32 accumulator occupies
+// TMEM columns 0 .. h_l - 1 (256 columns allocated).  All eight warps read
+// each accumulator back: warps w and w + 4 share TMEM lanes 32 (w % 4).. and
+// split the columns; each adds the bias, applies ReLU, rounds to BF16 and
+// writes the next layer's A operand.  The 5-wide head runs on CUDA cores, the
+// two halves' partial sums meeting in shared memory at the row's owner.
 namespace tcw {
 
-constexpr int kThreads = 128;
+constexpr int kRows = 128;                    // rows per MMA tile
+constexpr int kTiles = 2;                     // tiles per step, evaluated one after the other
+constexpr int kThreads = kRows * kTiles;      // thread t owns row t % 128 of tile t / 128
 constexpr int kTmemCols = 256;
+constexpr uint32_t kXTileBytes = kRows * kMlpK1 * 2;
+
+// Columns [lo, hi) of an N-column layer read back by warp half `half`
+// (warps 0-3 or 4-7; warps w and w + 4 see the same TMEM lane quadrant), in
+// units of 16 columns.
+__device__ __forceinline__ void col_range(int N, int half, int &lo, int &hi) {
+    const int u0 = ((N >> 4) + 1) >> 1;
+    lo = half ? 16 * u0 : 0;
+    hi = half ? N : 16 * u0;
+}
 
 __device__ __forceinline__ void put_bf16(unsigned char *base, uint32_t off, int row, int k, int K,
                                          __nv_bfloat16 v) {
@@ -394,24 +409,28 @@ __device__ __forceinline__ bool layer(unsigned char *base, const WideLayout &L, 
     return ok;
 }
 
-// BF16(ReLU(D + b)) of this thread's row into the next A operand (K = N):
-// 64 columns per TMEM wait, each 8-column core-matrix row one 16-byte store.
+// BF16(ReLU(D + b)) into the next A operand (K = N): this thread's row
+// (32 (warp % 4) + lane) and its warp half's columns; 64 columns per TMEM
+// wait, each 8-column core-matrix row one 16-byte store.
 __device__ __forceinline__ void relu_to_bf16(unsigned char *base, const WideLayout &L,
                                              uint32_t bias_off, uint32_t out_off, int N) {
+    const int warp = threadIdx.x >> 5;
     const uint32_t tmem = *reinterpret_cast<const uint32_t *>(base + L.tmem);
-    const uint32_t lane0 = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);
+    const uint32_t lane0 = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const float *b = reinterpret_cast<const float *>(base + bias_off);
-    const int row = threadIdx.x;
+    const int row = 32 * (warp & 3) + (threadIdx.x & 31);
+    int lo, hi;
+    col_range(N, warp >> 2, lo, hi);
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += 64) {
+    for (int c0 = lo; c0 < hi; c0 += 64) {
         uint32_t r[4][16];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (c0 + 16 * q < N) tc::ld16_nowait(lane0 + (uint32_t)(c0 + 16 * q), r[q]);
+            if (c0 + 16 * q < hi) tc::ld16_nowait(lane0 + (uint32_t)(c0 + 16 * q), r[q]);
         tc::ld_wait();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if (c0 + 16 * q >= N) break;
+            if (c0 + 16 * q >= hi) break;
 #pragma unroll
             for (int h = 0; h < 16; h += 8) {
                 const int c = c0 + 16 * q + h;
@@ -427,74 +446,92 @@ __device__ __forceinline__ void relu_to_bf16(unsigned char *base, const WideLayo
     }
 }
 
-// Writes this thread's 32 features (row threadIdx.x) as BF16.
+// Writes this thread's 32 features (tile threadIdx.x / 128, row
+// threadIdx.x % 128) as BF16.
 __device__ __forceinline__ void put_features(unsigned char *base, const WideLayout &L,
                                              const float (&f)[kMlpK1]) {
+    __nv_bfloat16 *x = reinterpret_cast<__nv_bfloat16 *>(base + L.x + (threadIdx.x / kRows) * kXTileBytes);
 #pragma unroll
     for (int k = 0; k < kMlpK1; k += 2)
-        tc::store_bf16x2(reinterpret_cast<__nv_bfloat16 *>(base + L.x),
-                         tc::core_off(threadIdx.x, k, kMlpK1), f[k], f[k + 1]);
+        tc::store_bf16x2(x, tc::core_off(threadIdx.x % kRows, k, kMlpK1), f[k], f[k + 1]);
 }
 
-// The MLP of the CTA's 128 rows; out = (phi-logit, o-logit, d_r, d_g, d_b)
-// of this thread's row, biases added.  All threads call it.
+// The MLP of the step's two tiles, one after the other, every warp reading
+// back its half of each layer's columns.  out = (phi-logit, o-logit, d_r,
+// d_g, d_b) of the thread's own row (tile threadIdx.x / 128), biases added.
+// All threads call it.
 __device__ __forceinline__ bool mlp_cta(unsigned char *base, const WideLayout &L, int h1, int h2,
                                         int h3, uint32_t &phase, float (&out)[5]) {
     bool ok = true;
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    ok &= layer(base, L, L.x, L.w1, kMlpK1, h1, phase);
-    relu_to_bf16(base, L, L.b1, L.a0, h1);
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    ok &= layer(base, L, L.a0, L.w2, h1, h2, phase);
-    relu_to_bf16(base, L, L.b2, L.a1, h2);
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    ok &= layer(base, L, L.a1, L.w3, h2, h3, phase);
-    // third hidden layer: BF16(ReLU(.)) in registers, then the head
+    const int warp = threadIdx.x >> 5, half = warp >> 2;
+    const int row = 32 * (warp & 3) + (threadIdx.x & 31);
     const uint32_t tmem = *reinterpret_cast<const uint32_t *>(base + L.tmem);
-    const uint32_t lane0 = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);
+    const uint32_t lane0 = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const float *b3 = reinterpret_cast<const float *>(base + L.b3);
     const float *head = reinterpret_cast<const float *>(base + L.head);
     const float *b4 = reinterpret_cast<const float *>(base + L.b4);
-    float acc[kMlpOut];
-#pragma unroll
-    for (int k = 0; k < kMlpOut; ++k) acc[k] = b4[k];
+    float *red = reinterpret_cast<float *>(base + L.red) + row * 8;
+    int lo3, hi3;
+    col_range(h3, half, lo3, hi3);
 #pragma unroll 1
-    for (int c0 = 0; c0 < h3; c0 += 64) {
-        uint32_t r[4][16];
+    for (int t = 0; t < kTiles; ++t) {
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        ok &= layer(base, L, L.x + (uint32_t)t * kXTileBytes, L.w1, kMlpK1, h1, phase);
+        relu_to_bf16(base, L, L.b1, L.a0, h1);
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        ok &= layer(base, L, L.a0, L.w2, h1, h2, phase);
+        relu_to_bf16(base, L, L.b2, L.a1, h2);
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        ok &= layer(base, L, L.a1, L.w3, h2, h3, phase);
+        // third hidden layer BF16(ReLU(.)) in registers, then this half's
+        // share of the head; the row's owner (warp half t) adds the other's
+        float acc[kMlpOut] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int c0 = lo3; c0 < hi3; c0 += 64) {
+            uint32_t r[4][16];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (c0 + 16 * q < h3) tc::ld16_nowait(lane0 + (uint32_t)(c0 + 16 * q), r[q]);
-        tc::ld_wait();
+            for (int q = 0; q < 4; ++q)
+                if (c0 + 16 * q < hi3) tc::ld16_nowait(lane0 + (uint32_t)(c0 + 16 * q), r[q]);
+            tc::ld_wait();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (c0 + 16 * q >= h3) break;
+            for (int q = 0; q < 4; ++q) {
+                if (c0 + 16 * q >= hi3) break;
 #pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-                const int c = c0 + 16 * q + i;
-                const uint32_t hp = tc::relu_bf16x2(__uint_as_float(r[q][i]) + b3[c],
-                                                    __uint_as_float(r[q][i + 1]) + b3[c + 1]);
+                for (int i = 0; i < 16; i += 2) {
+                    const int c = c0 + 16 * q + i;
+                    const uint32_t hp = tc::relu_bf16x2(__uint_as_float(r[q][i]) + b3[c],
+                                                        __uint_as_float(r[q][i + 1]) + b3[c + 1]);
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const float h = j ? tc::bf16_hi(hp) : tc::bf16_lo(hp);
-                    const float4 w = *reinterpret_cast<const float4 *>(head + (c + j) * 8);
-                    const float w4 = head[(c + j) * 8 + 4];
-                    acc[0] = fmaf(w.x, h, acc[0]);
-                    acc[1] = fmaf(w.y, h, acc[1]);
-                    acc[2] = fmaf(w.z, h, acc[2]);
-                    acc[3] = fmaf(w.w, h, acc[3]);
-                    acc[4] = fmaf(w4, h, acc[4]);
+                    for (int j = 0; j < 2; ++j) {
+                        const float h = j ? tc::bf16_hi(hp) : tc::bf16_lo(hp);
+                        const float4 w = *reinterpret_cast<const float4 *>(head + (c + j) * 8);
+                        const float w4 = head[(c + j) * 8 + 4];
+                        acc[0] = fmaf(w.x, h, acc[0]);
+                        acc[1] = fmaf(w.y, h, acc[1]);
+                        acc[2] = fmaf(w.z, h, acc[2]);
+                        acc[3] = fmaf(w.w, h, acc[3]);
+                        acc[4] = fmaf(w4, h, acc[4]);
+                    }
                 }
             }
         }
-    }
+        if (half != t) {
 #pragma unroll
-    for (int k = 0; k < kMlpOut; ++k) out[k] = acc[k];
+            for (int k = 0; k < kMlpOut; ++k) red[k] = acc[k];
+        }
+        tc::fence_before();
+        __syncthreads();
+        if (half == t) {
+#pragma unroll
+            for (int k = 0; k < kMlpOut; ++k) out[k] = b4[k] + acc[k] + red[k];
+        }
+    }
     tc::fence_before();
     __syncthreads();
     return ok;
