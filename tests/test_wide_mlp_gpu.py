@@ -42,6 +42,25 @@ def test_paper_width_mlp_matches_oracle(R, n, prec, res, W, H):
     assert np.abs(out["rgb"].cpu().numpy() - ref["rgb"]).max() <= 2e-3
 
 
+@pytest.mark.parametrize("hidden", [(48, 80, 16), (16, 112, 48)])
+def test_uneven_widths_match_oracle(R, hidden):
+    """Widths with an odd number of 16-column units: the two warp halves that
+    read each layer back split its columns unevenly (one half has none at
+    width 16); 5,003 Gaussians leave the last 256-row step ragged."""
+    scene = synth.unbounded_scene(5003, seed=121, precision="fp16")
+    scene.mlp = synth.random_mlp(122, hidden=hidden)
+    cam = synth.orbit_cameras(8, 8.0, 1.0, 144, 96, 60.0)[3]
+    h = R.load_scene(scene)
+    try:
+        out = R.render(h, cam, use_mlp=True, rgb_residual=True, count=True)
+    finally:
+        R.unload_scene(h)
+    ref = oracle.render(scene.attrs, cam, mlp=scene.mlp, use_mlp=True, rgb_residual=True,
+                        want_count=True)
+    np.testing.assert_array_equal(out["count"].cpu().numpy(), ref["count"])
+    assert np.abs(out["rgb"].cpu().numpy() - ref["rgb"]).max() <= 2e-3
+
+
 def test_paper_width_mlp_differs_from_small_mlp(R):
     """Sanity: the three-layer MLP is actually used (different image)."""
     scene = synth.unbounded_scene(8000, seed=5, precision="fp16")
