@@ -214,7 +214,10 @@ mgs_status mgs_render_checked(mgs_workspace ws, mgs_scene scene,
  * colour image into out_rgb (as mgs_render) and the depth-aware weighted mean
  * view depth D = sum d_i a_i w_i / sum a_i w_i (Eq. 2's weights; 0 where no
  * Gaussian is included) into out_depth (device, height x width FP32).  The
- * sums use FP32 FMAs for every precision.  MGS_FLAG_SORTED is not accepted.
+ * colour image equals mgs_render's with the same options.  The numerator
+ * sum d a w is FP32; the denominator sum a w is FP32 for FP32 attributes
+ * (or MGS_FLAG_RASTER_FMA) and the tensor-core B of the colour image for
+ * FP16 attributes.  MGS_FLAG_SORTED is not accepted.
  * Errors: MGS_ERR_INVALID_ARG for a NULL out_depth, otherwise as mgs_render. */
 mgs_status mgs_render_depth(mgs_workspace ws, mgs_scene scene,
                             const mgs_camera *cam, const mgs_render_opts *opts,

@@ -136,10 +136,12 @@ struct RenderArgs {
 };
 
 // Does this render rasterise with tensor-core sums (FP16 attributes, no
-// comparator, no depth image, not forced onto the FMA pipe)?  Binning then
-// also converts every visible Gaussian's weights to FP16 (args.wt16).
+// comparator, not forced onto the FMA pipe)?  Binning then also converts
+// every visible Gaussian's weights to FP16 (args.wt16).  A depth image
+// rendered this way takes its numerator sum d a w in FP32 and its
+// denominator from the tensor-core B.
 __host__ __device__ inline bool tc_raster(const RenderArgs &a) {
-    return a.precision == MGS_PREC_FP16 && a.out_depth == nullptr &&
+    return a.precision == MGS_PREC_FP16 &&
            (a.flags & (MGS_FLAG_RASTER_FMA | MGS_FLAG_SORTED)) == 0;
 }
 

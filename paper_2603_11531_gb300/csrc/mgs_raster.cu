@@ -245,6 +245,7 @@ constexpr int kRing = 40;        // candidate slots per warp: five chunks
 struct TcSmem {
     float4 geo[kTcWarps][3][kRing / 2];
     uint4 wt[kTcWarps][kRing];            // slot s: its 8 FP16 weight columns
+    float2 wd[kTcWarps][kRing / 2];       // depth image only: w d of slots 2p, 2p + 1
 };
 
 __device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
@@ -263,11 +264,16 @@ __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, 
 // One chunk of 8 candidates starting at ring slot c0 (a multiple of 8): the
 // lane's entries 2t, 2t + 1 at its eight pixels (same FP32 sequence as
 // accumulate()), T updated, alphas packed to FP16 and summed by four MMAs.
-template <bool kCount, bool kClamp>
+// kDepth: also AD[j] += (a, b) * (w d of the two entries), the FP32 numerator
+// of the depth image (Eq. 5), kept as two partial sums per pixel.
+template <bool kCount, bool kClamp, bool kDepth = false>
 __device__ __forceinline__ void tc_chunk(const float4 (*geo)[kRing / 2], const uint4 *wt,
                                          int c0, int g, int t, const f2 (&pxc)[8], f2 pyc,
-                                         f2 kq2, float (&T)[8], float (&D)[4][4], int (&cnt)[8]) {
+                                         f2 kq2, float (&T)[8], float (&D)[4][4], int (&cnt)[8],
+                                         const float2 *wd = nullptr, f2 *AD = nullptr) {
     const int pr = (c0 >> 1) + t;
+    f2 wdp = 0ull;
+    if constexpr (kDepth) wdp = pk(wd[pr].x, wd[pr].y);
     const float4 q0 = geo[0][pr], q1 = geo[1][pr], q2 = geo[2][pr];
     const f2 mx = pk(q0.x, q0.y), my = pk(q0.z, q0.w);
     const f2 l11 = pk(q1.x, q1.y), l21 = pk(q1.z, q1.w);
@@ -296,6 +302,7 @@ __device__ __forceinline__ void tc_chunk(const float4 (*geo)[kRing / 2], const u
         if (kCount) cnt[j] += (qa <= 9.0f) + (qb <= 9.0f);
         T[j] = fmaf(-aa, T[j], T[j]);
         T[j] = fmaf(-ab, T[j], T[j]);
+        if constexpr (kDepth) AD[j] = fma2(pk(aa, ab), wdp, AD[j]);
         a[j] = h2bits(aa, ab);            // k = 2t (low half), 2t + 1
     }
     const unsigned short *wa = reinterpret_cast<const unsigned short *>(wt + c0 + 2 * t);
@@ -304,7 +311,7 @@ __device__ __forceinline__ void tc_chunk(const float4 (*geo)[kRing / 2], const u
     for (int i = 0; i < 4; ++i) mma_k8(D[i], a[2 * i], a[2 * i + 1], b0);   // pixels 2i, 2i + 1
 }
 
-template <bool kAux, bool kCount>
+template <bool kAux, bool kCount, bool kDepth = false>
 __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile, TcSmem &sm) {
     const DevCamera &cam = args.cam;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
@@ -315,6 +322,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     const int py = by0 + g;
     float4(*geo)[kRing / 2] = sm.geo[warp];
     uint4 *wt = sm.wt[warp];
+    float2 *wd = sm.wd[warp];
 
     const uint32_t start = args.tile_offsets[tile];
     const uint32_t end = args.tile_offsets[tile + 1];
@@ -334,10 +342,12 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     float T[8];
     float D[4][4];
     int cnt[8];
+    f2 AD[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         T[j] = 1.0f;
         cnt[j] = 0;
+        AD[j] = 0ull;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) D[i][0] = D[i][1] = D[i][2] = D[i][3] = 0.0f;
@@ -348,17 +358,20 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 b_n = make_float2(0.f, 0.f);
     uint4 w_n = make_uint4(0u, 0u, 0u, 0u);
+    float2 d_n = make_float2(0.f, 0.f);   // depth image: (-w, view depth)
     if (start + lane < end) {
         const uint32_t gid = __ldg(&args.gids[start + lane]);
         a_n = __ldg(&args.rec[gid].a);
         b_n = __ldg(reinterpret_cast<const float2 *>(&args.rec[gid].b));
         w_n = __ldg(&args.wt16[gid]);
+        if constexpr (kDepth) d_n = make_float2(__ldg(&args.rec[gid].b.z), __ldg(&args.rec[gid].c.z));
     }
     for (uint32_t base = start; base < end; base += 32) {
         const uint32_t j = base + lane;
         const float4 a = a_n;
         const float2 b = b_n;
         const uint4 wv = w_n;
+        const float2 dv = d_n;
         const bool cand =
             j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bcx, bcy, 3.5f, 3.5f));
         if (j + 32 < end) {
@@ -366,6 +379,8 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             a_n = __ldg(&args.rec[gid].a);
             b_n = __ldg(reinterpret_cast<const float2 *>(&args.rec[gid].b));
             w_n = __ldg(&args.wt16[gid]);
+            if constexpr (kDepth)
+                d_n = make_float2(__ldg(&args.rec[gid].b.z), __ldg(&args.rec[gid].c.z));
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         bool clamp = false;
@@ -384,6 +399,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             q[2 + o] = b.y;
             clamp = b.y > kLogClamp;
             wt[pos] = wv;                        // FP16 weights prepared during binning
+            if constexpr (kDepth) reinterpret_cast<float *>(&wd[pos >> 1])[o] = -dv.x * dv.y;
         }
         // slots of this batch that need the 0.99 clamp
         const unsigned cb = __ballot_sync(0xffffffffu, clamp);
@@ -398,9 +414,9 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
         count += __popc(bal);
         while (count >= kChunk) {
             if ((clamp_mask >> head) & 0xFFull)
-                tc_chunk<kCount, true>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+                tc_chunk<kCount, true, kDepth>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt, wd, AD);
             else
-                tc_chunk<kCount, false>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+                tc_chunk<kCount, false, kDepth>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt, wd, AD);
             clamp_mask &= ~(0xFFull << head);
             head = head + kChunk == kRing ? 0 : head + kChunk;
             count -= kChunk;
@@ -422,12 +438,13 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             q[o] = 1.0f;
             q[2 + o] = 0.0f;
             wt[pos] = make_uint4(0u, 0u, 0u, 0u);
+            if constexpr (kDepth) reinterpret_cast<float *>(&wd[pos >> 1])[o] = 0.0f;
         }
         __syncwarp();
         if ((clamp_mask >> head) & 0xFFull)
-            tc_chunk<kCount, true>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+            tc_chunk<kCount, true, kDepth>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt, wd, AD);
         else
-            tc_chunk<kCount, false>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt);
+            tc_chunk<kCount, false, kDepth>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt, wd, AD);
     }
 
     // Quad reduction: columns c and c + 4 (lanes t, t ^ 2), then swap halves
@@ -442,8 +459,16 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int k = 0; k < 4; ++k) o[i][k] = __shfl_xor_sync(0xffffffffu, v[i][k], 1);
+    float ad[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
+        if constexpr (kDepth) {
+            float x, y;
+            upk(AD[k], x, y);
+            ad[k] = x + y;
+            ad[k] += __shfl_xor_sync(0xffffffffu, ad[k], 1);
+            ad[k] += __shfl_xor_sync(0xffffffffu, ad[k], 2);
+        }
         T[k] *= __shfl_xor_sync(0xffffffffu, T[k], 1);
         T[k] *= __shfl_xor_sync(0xffffffffu, T[k], 2);
         if (kCount) {
@@ -482,6 +507,8 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
                 args.out_aux[4 * HW + p] = tr;
             }
             if (kCount) args.out_count[p] = cnt[2 * i + h];
+            // FP32 numerator over the tensor-core B (both unscaled)
+            if (kDepth) args.out_depth[p] = bb > 0.0f ? ad[2 * i + h] / bb : 0.0f;
         }
     }
 }
@@ -498,11 +525,11 @@ __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
     raster_tile<kAux, kCount, kDepth>(args, (int)args.tile_order[blockIdx.x], buf);
 }
 
-template <bool kAux, bool kCount>
+template <bool kAux, bool kCount, bool kDepth = false>
 __global__ void __launch_bounds__(kTcThreads) k_raster_tc(RenderArgs args) {
     __shared__ TcSmem sm;
     if (args.status->last_pairs > args.capacity) return;  // overflowed: lists incomplete
-    raster_tile_tc<kAux, kCount>(args, (int)args.tile_order[blockIdx.x], sm);
+    raster_tile_tc<kAux, kCount, kDepth>(args, (int)args.tile_order[blockIdx.x], sm);
 }
 
 // Persistent, batched: the tiles of several views (different scenes and
@@ -556,8 +583,11 @@ cudaError_t launch_t(const RenderArgs &a, cudaStream_t stream) {
 
 cudaError_t launch_raster(const RenderArgs &a, cudaStream_t stream) {
     const bool aux = a.out_aux != nullptr, cnt = a.out_count != nullptr;
-    if (a.out_depth) {   // depth image (Eq. 5): FMA sums, no aux / count outputs
-        k_raster<false, false, true><<<a.cam.tiles_x * a.cam.tiles_y, kThreads, 0, stream>>>(a);
+    if (a.out_depth) {   // depth image (Eq. 5), no aux / count outputs
+        if (use_tc(a))
+            k_raster_tc<false, false, true><<<a.cam.tiles_x * a.cam.tiles_y, kTcThreads, 0, stream>>>(a);
+        else
+            k_raster<false, false, true><<<a.cam.tiles_x * a.cam.tiles_y, kThreads, 0, stream>>>(a);
         return cudaGetLastError();
     }
     if (aux && cnt) return launch_t<true, true>(a, stream);
