@@ -98,7 +98,7 @@ struct DevStatus {
 // rasteriser:
 //   a = (m_x, m_y, l11, l21)          FP32-contract mean and factors
 //   b = (l22, log2 o, -w, -w c_r)
-//   c = (-w c_g, -w c_b, view depth (FP32 contract), 0)
+//   c = (-w c_g, -w c_b, view depth d (FP32 contract), -w d)
 // The inclusion test is q = (l11 dx + l21 dy)^2 + (l22 dy)^2 <= 9 with
 // dx = x + 0.5 - m_x, dy = y + 0.5 - m_y, evaluated exactly as
 // e1 = fma(l11, dx, l21*dy), e2 = l22*dy, q = fma(e1, e1, e2*e2).

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kWide ? tcw::kThreads : (kTC ? tc::kThreads : 
         ProjRec r;
         r.a = make_float4(c.mx, c.my, c.l11, c.l21);
         r.b = make_float4(c.l22, __log2f(opa), -w, -w * rgb[0]);
-        r.c = make_float4(-w * rgb[1], -w * rgb[2], c.tz, 0.f);
+        r.c = make_float4(-w * rgb[1], -w * rgb[2], c.tz, -w * c.tz);
         args.rec[i] = r;
         args.rect[i] = make_uint2((unsigned)c.rect[0] | ((unsigned)c.rect[2] << 16),
                                   (unsigned)c.rect[1] | ((unsigned)c.rect[3] << 16));

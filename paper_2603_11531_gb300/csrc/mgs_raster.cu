@@ -168,10 +168,7 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
             wb[2][pos] = make_ulonglong2(pk(b.x, b.x), pk(b.y, b.y));
             wb[3][pos] = make_ulonglong2(pk(b.z, b.z), pk(b.w, b.w));
             wb[4][pos] = make_ulonglong2(pk(c.x, c.x), pk(c.y, c.y));
-            if (kDepth) {
-                const float wd = b.z * c.z;   // -w d
-                wb[5][pos] = make_ulonglong2(pk(wd, wd), 0ull);
-            }
+            if (kDepth) wb[5][pos] = make_ulonglong2(pk(c.w, c.w), 0ull);   // -w d
         }
         __syncwarp();
         const int nc = __popc(bal);
@@ -358,20 +355,20 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 b_n = make_float2(0.f, 0.f);
     uint4 w_n = make_uint4(0u, 0u, 0u, 0u);
-    float2 d_n = make_float2(0.f, 0.f);   // depth image: (-w, view depth)
+    float d_n = 0.f;                      // depth image: -w d
     if (start + lane < end) {
         const uint32_t gid = __ldg(&args.gids[start + lane]);
         a_n = __ldg(&args.rec[gid].a);
         b_n = __ldg(reinterpret_cast<const float2 *>(&args.rec[gid].b));
         w_n = __ldg(&args.wt16[gid]);
-        if constexpr (kDepth) d_n = make_float2(__ldg(&args.rec[gid].b.z), __ldg(&args.rec[gid].c.z));
+        if constexpr (kDepth) d_n = __ldg(&args.rec[gid].c.w);
     }
     for (uint32_t base = start; base < end; base += 32) {
         const uint32_t j = base + lane;
         const float4 a = a_n;
         const float2 b = b_n;
         const uint4 wv = w_n;
-        const float2 dv = d_n;
+        const float dv = d_n;
         const bool cand =
             j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bcx, bcy, 3.5f, 3.5f));
         if (j + 32 < end) {
@@ -379,8 +376,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             a_n = __ldg(&args.rec[gid].a);
             b_n = __ldg(reinterpret_cast<const float2 *>(&args.rec[gid].b));
             w_n = __ldg(&args.wt16[gid]);
-            if constexpr (kDepth)
-                d_n = make_float2(__ldg(&args.rec[gid].b.z), __ldg(&args.rec[gid].c.z));
+            if constexpr (kDepth) d_n = __ldg(&args.rec[gid].c.w);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         bool clamp = false;
@@ -399,7 +395,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             q[2 + o] = b.y;
             clamp = b.y > kLogClamp;
             wt[pos] = wv;                        // FP16 weights prepared during binning
-            if constexpr (kDepth) reinterpret_cast<float *>(&wd[pos >> 1])[o] = -dv.x * dv.y;
+            if constexpr (kDepth) reinterpret_cast<float *>(&wd[pos >> 1])[o] = -dv;
         }
         // slots of this batch that need the 0.99 clamp
         const unsigned cb = __ballot_sync(0xffffffffu, clamp);
