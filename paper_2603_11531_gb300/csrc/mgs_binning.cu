@@ -13,7 +13,8 @@
 //   1. k_bin_count: each CTA counts the pairs of its warps' shares into a
 //      shared-memory histogram over the tiles; one global atomicAdd per (CTA,
 //      tile) reserves the CTA's block inside the tile and returns its base.
-//   2. k_scan: exclusive scan of the per-tile totals -> tile offsets.
+//   2. k_scan_order: exclusive scan of the per-tile totals -> tile offsets,
+//      and the rasterisation order (longest lists first).
 //   3. k_bin_scatter: the same CTA re-expands the same pairs and places each
 //      one at offset[tile] + base[c][tile] + (shared-memory rank).
 //
@@ -323,15 +324,28 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_scatter(
     }
 }
 
-// Exclusive scan of tile_count[T] into tile_offsets[T+1], by one block; also
-// records the pair count and flags capacity overflow.
-__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restrict__ count,
-                                                       uint32_t *__restrict__ offsets, int T,
-                                                       uint64_t capacity, DevStatus *status) {
+// One block over the per-tile totals:
+//   * exclusive scan of tile_count[T] into tile_offsets[T+1]; records the
+//     pair count and flags capacity overflow;
+//   * rasterisation order: tiles by decreasing list length (bucketed by
+//     floor(log2(length))), so the longest tiles start first and the tail of
+//     the raster launch is made of short tiles;
+//   * hands this frame's weight bound to the rasteriser and resets the
+//     accumulator for the next frame.
+__global__ void __launch_bounds__(kScanThreads) k_scan_order(const uint32_t *__restrict__ count,
+                                                             uint32_t *__restrict__ offsets,
+                                                             uint32_t *__restrict__ order, int T,
+                                                             uint64_t capacity, DevStatus *status) {
     __shared__ unsigned long long warp_sums[kScanThreads / 32];
     __shared__ unsigned long long carry;
+    __shared__ uint32_t hist[33], start[33];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry = 0;
+    if (tid == 0) {
+        carry = 0;
+        status->wmax_frame_bits = status->wmax_bits;
+        status->wmax_bits = 0u;
+    }
+    if (tid < 33) hist[tid] = 0u;
     __syncthreads();
     for (int base = 0; base < T; base += kScanThreads * 4) {
         const int i0 = base + tid * 4;
@@ -340,6 +354,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
         for (int k = 0; k < 4; ++k) {
             v[k] = (i0 + k < T) ? count[i0 + k] : 0u;
             local += v[k];
+            if (i0 + k < T) {
+                const uint32_t c = (uint32_t)v[k];
+                atomicAdd(&hist[c ? 32 - __clz(c) : 0], 1u);   // bucket 0 (empty) .. 32
+            }
         }
         unsigned long long incl = local;
 #pragma unroll
@@ -350,13 +368,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
         if (lane == 31) warp_sums[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            unsigned long long s = warp_sums[lane];
+            unsigned long long sw = warp_sums[lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
+                unsigned long long y = __shfl_up_sync(0xffffffffu, sw, o);
+                if (lane >= o) sw += y;
             }
-            warp_sums[lane] = s;
+            warp_sums[lane] = sw;
         }
         __syncthreads();
         unsigned long long run = carry + (incl - local) + (warp > 0 ? warp_sums[warp - 1] : 0ull);
@@ -375,42 +393,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
         status->last_pairs = K;
         atomicMax(&status->max_pairs, K);
         if (K > capacity || K > 0xFFFFFFFFull) atomicOr(&status->overflow, kStatusOverflow);
-    }
-}
-
-// Rasterisation order: tiles by decreasing list length (bucketed by
-// floor(log2(length))), so the longest tiles start first and the tail of the
-// launch is made of short tiles.  One block.  Also hands this frame's weight
-// bound to the rasteriser and resets the accumulator for the next frame.
-__global__ void __launch_bounds__(kScanThreads) k_tile_order(const uint32_t *__restrict__ count,
-                                                             int T, uint32_t *__restrict__ order,
-                                                             DevStatus *status) {
-    __shared__ uint32_t hist[33], start[33];
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        status->wmax_frame_bits = status->wmax_bits;
-        status->wmax_bits = 0u;
-    }
-    if (tid < 33) hist[tid] = 0u;
-    __syncthreads();
-    for (int t = tid; t < T; t += blockDim.x) {
-        const uint32_t c = count[t];
-        const int b = c ? 32 - __clz(c) : 0;      // 0 (empty) .. 32
-        atomicAdd(&hist[b], 1u);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t run = 0;
-        for (int b = 32; b >= 0; --b) {          // longest bucket first
-            start[b] = run;
-            run += hist[b];
+        uint32_t r = 0;
+        for (int bk = 32; bk >= 0; --bk) {      // longest bucket first
+            start[bk] = r;
+            r += hist[bk];
         }
     }
     __syncthreads();
     for (int t = tid; t < T; t += blockDim.x) {
         const uint32_t c = count[t];
-        const int b = c ? 32 - __clz(c) : 0;
-        order[atomicAdd(&start[b], 1u)] = (uint32_t)t;
+        order[atomicAdd(&start[c ? 32 - __clz(c) : 0], 1u)] = (uint32_t)t;
     }
 }
 
@@ -462,9 +454,8 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch,
                                                       groups, a.tile_count, bases);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_scan<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, T, a.capacity, a.status);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_tile_order<<<1, kScanThreads, 0, stream>>>(a.tile_count, T, a.tile_order, a.status);
+    k_scan_order<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, a.tile_order, T,
+                                                 a.capacity, a.status);
     if ((e = cudaGetLastError()) != cudaSuccess || a.n == 0) return e;
     k_bin_scatter<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, excl, groups,
                                                     a.tile_offsets, bases, a.gids, a.capacity,

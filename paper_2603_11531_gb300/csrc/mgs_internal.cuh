@@ -89,7 +89,7 @@ struct DevStatus {
     // Largest |w c| and w over the visible Gaussians (FP32 bits; positive
     // floats order as unsigned integers): accumulated by preprocessing,
     // handed to the frame's rasteriser (wmax_frame_bits) and reset by
-    // k_tile_order, which runs between the two.
+    // k_scan_order, which runs between the two.
     unsigned int wmax_bits;
     unsigned int wmax_frame_bits;
 };
