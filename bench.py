@@ -163,6 +163,13 @@ def cpu_baseline_sample(tile_stride: int = 8, pose: int = 0):
             "seconds": (t1 - t0) + t_r}
 
 
+# Kernels of this library one FP16 render launches: k_preprocess,
+# k_group_pairs, k_bin_plan, k_bin_count, k_scan_order, k_bin_scatter and
+# k_raster_tc, once each (the tile-count memset is not a kernel).  The ncu
+# launch list of a bench run shows the same set per frame.
+KERNELS_PER_FRAME = 7
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -330,7 +337,7 @@ def run_gpu(args):
                          "stage_ms_per_frame": {"preprocess_mlp": stage_per_frame[0],
                                                 "binning": stage_per_frame[1],
                                                 "raster": stage_per_frame[2]}},
-            "gpu_launches": 6 * N_POSES * args.steps,
+            "gpu_launches": KERNELS_PER_FRAME * N_POSES * args.steps,
             "clocks": clocks,
             "peaks": peaks_kind,
         }
