@@ -299,3 +299,20 @@ def test_binning_work_plan_cases(R):
     out, ref = _render_both(R, synth.Scene(big), cam)
     np.testing.assert_array_equal(out["count"], ref["count"])
     assert np.abs(out["rgb"] - ref["rgb"]).max() <= TOL_FP32
+
+
+@pytest.mark.parametrize("prec,use_mlp,tol", [("fp32", False, TOL_FP32), ("fp16", True, TOL_FP16_MLP)])
+def test_two_tile_bands(R, prec, use_mlp, tol):
+    """4096x2304 has 36,864 tiles, more than one shared-memory band of the
+    binning histograms (32,768 tiles): both bands hold listed pairs (means
+    spread over [-3, 3]^3 reach the bottom tile rows)."""
+    sc = synth.uniform_scene(3000, seed=61, precision=prec)
+    a = sc.attrs.copy()
+    a[:, 0:3] *= 3.0
+    scene = synth.Scene(a)
+    scene.mlp = synth.random_mlp(62)
+    cam = synth.look_at((0, 0, -10), (0, 0, 0), 4096, 2304, 60.0)
+    out, ref = _render_both(R, scene, cam, use_mlp=use_mlp, bg=(0.1, 0.2, 0.3))
+    assert int(ref["offsets"][-1] - ref["offsets"][32768]) > 0
+    np.testing.assert_array_equal(out["count"], ref["count"])
+    assert np.abs(out["rgb"] - ref["rgb"]).max() <= tol
