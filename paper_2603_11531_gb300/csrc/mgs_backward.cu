@@ -219,16 +219,21 @@ constexpr int kDxS = 24;
 constexpr int kOnesCol = kMlpHidden;  // h1 column 64 holds 1: its products give dL/db2
 constexpr int kXOnesCol = kMlpIn;     // x column 22 holds 1: its products give dL/db1
 
+// About 108 KB, two CTAs per SM: d1 overwrites d2 once the products that
+// need d2 are done, and dx reuses h2's space once h2 is no longer read.
 struct BwdSmem {
     MlpSmem mlp;                          // weights, BF16 features x, head outputs
     __nv_bfloat16 h1[kRows * kHStride];   // BF16 hidden activations (forward recompute)
-    __nv_bfloat16 h2[kRows * kHStride];
-    float d2[kRows * kDS];                // dL/d(pre-activation 2)
-    float d1[kRows * kDS];                // dL/d(pre-activation 1)
+    union {
+        __nv_bfloat16 h2[kRows * kHStride];
+        float dx[kRows * kDxS];           // dL/d(features), staged for the row threads
+    };
+    float dd[kRows * kDS];                // dL/d(pre-activation 2), then of pre-activation 1
     float d3[kRows * kD3S];               // dL/d(head outputs), columns 5..7 zero
-    float dx[kRows * kDxS];               // dL/d(features), staged for the row threads
     float b3[kMlpThreads / 32][8];        // per-warp sums of d3
 };
+static_assert(kRows * kDxS * sizeof(float) <= kRows * kHStride * sizeof(__nv_bfloat16),
+              "dx fits in h2's space");
 
 // Weight-gradient accumulators of one lane (m16n8 fragments): warp w owns
 // rows 16w..16w+15 of dW2 (nine n-tiles, the last one the b2 column), of dW1
@@ -265,49 +270,61 @@ __device__ __forceinline__ float2 relu_mask(const __nv_bfloat16 *h, float a, flo
     return make_float2(__low2float(m) > 0.0f ? a : 0.0f, __high2float(m) > 0.0f ? b : 0.0f);
 }
 
-// Deltas of the Eq. 4 MLP for the warp's 32 rows (d3 already in shared
-// memory):  d2 = (d3 W3) * [h2 > 0],  d1 = (d2 W2) * [h1 > 0],  dx = d1 W1.
-// d2 and d1 stay in shared memory for the weight gradients; dx is staged for
-// the row threads.  The d1 accumulators serve directly as the A fragments of
-// dx = d1 W1, taking k = 2t and 2t + 1 of each step for fragment columns t
-// and t + 4 (B rows follow the same order).
-__device__ __forceinline__ void mlp_deltas_warp(BwdSmem &sm, int warp, int lane) {
+// The adjoint of the Eq. 4 MLP for the CTA's 128 rows (d3 in shared memory)
+// runs in four steps, with a CTA barrier after each of the first three:
+//   1. mlp_d2_warp      d2 = (d3 W3) * [h2 > 0] for the warp's 32 rows;
+//   2. mlp_wgrad2_cta   dW2 += d2^T [h1 | 1] and dW3^T += h2^T d3;
+//   3. mlp_d1_warp      d1 = (d2 W2) * [h1 > 0] over d2 in place and
+//                       dx = d1 W1 into h2's space, for the warp's rows;
+//   4. mlp_wgrad1_cta   dW1 += d1^T [x | 1].
+// TF32 products, FP32 accumulation.
+
+__device__ __forceinline__ void mlp_d2_warp(BwdSmem &sm, int warp, int lane) {
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll 1
     for (int mt = 0; mt < 2; ++mt) {
         const int r0 = warp * 32 + mt * 16 + g, r1 = r0 + 8;
-        {
-            const uint32_t a0 = to_tf32(sm.d3[r0 * kD3S + t]), a1 = to_tf32(sm.d3[r1 * kD3S + t]);
-            const uint32_t a2 = to_tf32(sm.d3[r0 * kD3S + t + 4]);
-            const uint32_t a3 = to_tf32(sm.d3[r1 * kD3S + t + 4]);
+        const uint32_t a0 = to_tf32(sm.d3[r0 * kD3S + t]), a1 = to_tf32(sm.d3[r1 * kD3S + t]);
+        const uint32_t a2 = to_tf32(sm.d3[r0 * kD3S + t + 4]);
+        const uint32_t a3 = to_tf32(sm.d3[r1 * kD3S + t + 4]);
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                float c[4] = {0.f, 0.f, 0.f, 0.f};
-                mma_tf32(c, a0, a1, a2, a3, bf_tf32(&sm.mlp.w3[t * kW2Stride + nt * 8 + g]),
-                         bf_tf32(&sm.mlp.w3[(t + 4) * kW2Stride + nt * 8 + g]));
-                const int col = nt * 8 + 2 * t;
-                *reinterpret_cast<float2 *>(&sm.d2[r0 * kDS + col]) =
-                    relu_mask(&sm.h2[r0 * kHStride + col], c[0], c[1]);
-                *reinterpret_cast<float2 *>(&sm.d2[r1 * kDS + col]) =
-                    relu_mask(&sm.h2[r1 * kHStride + col], c[2], c[3]);
-            }
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_tf32(c, a0, a1, a2, a3, bf_tf32(&sm.mlp.w3[t * kW2Stride + nt * 8 + g]),
+                     bf_tf32(&sm.mlp.w3[(t + 4) * kW2Stride + nt * 8 + g]));
+            const int col = nt * 8 + 2 * t;
+            *reinterpret_cast<float2 *>(&sm.dd[r0 * kDS + col]) =
+                relu_mask(&sm.h2[r0 * kHStride + col], c[0], c[1]);
+            *reinterpret_cast<float2 *>(&sm.dd[r1 * kDS + col]) =
+                relu_mask(&sm.h2[r1 * kHStride + col], c[2], c[3]);
         }
-        __syncwarp();
+    }
+}
+
+// The d1 accumulators serve directly as the A fragments of dx = d1 W1,
+// taking k = 2t and 2t + 1 of each step for fragment columns t and t + 4
+// (B rows follow the same order).
+__device__ __forceinline__ void mlp_d1_warp(BwdSmem &sm, int warp, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = warp * 32 + mt * 16 + g, r1 = r0 + 8;
         float c[8][4];
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
 #pragma unroll
         for (int ks = 0; ks < 8; ++ks) {
             const int k0 = ks * 8;
-            const uint32_t a0 = to_tf32(sm.d2[r0 * kDS + k0 + t]);
-            const uint32_t a1 = to_tf32(sm.d2[r1 * kDS + k0 + t]);
-            const uint32_t a2 = to_tf32(sm.d2[r0 * kDS + k0 + t + 4]);
-            const uint32_t a3 = to_tf32(sm.d2[r1 * kDS + k0 + t + 4]);
+            const uint32_t a0 = to_tf32(sm.dd[r0 * kDS + k0 + t]);
+            const uint32_t a1 = to_tf32(sm.dd[r1 * kDS + k0 + t]);
+            const uint32_t a2 = to_tf32(sm.dd[r0 * kDS + k0 + t + 4]);
+            const uint32_t a3 = to_tf32(sm.dd[r1 * kDS + k0 + t + 4]);
 #pragma unroll
             for (int nt = 0; nt < 8; ++nt)
                 mma_tf32(c[nt], a0, a1, a2, a3, bf_tf32(&sm.mlp.w2[(k0 + t) * kW2Stride + nt * 8 + g]),
                          bf_tf32(&sm.mlp.w2[(k0 + t + 4) * kW2Stride + nt * 8 + g]));
         }
+        __syncwarp();   // every lane has read this m-tile's d2 rows: overwrite them with d1
         float dx[3][4];
 #pragma unroll
         for (int ft = 0; ft < 3; ++ft) dx[ft][0] = dx[ft][1] = dx[ft][2] = dx[ft][3] = 0.f;
@@ -316,8 +333,8 @@ __device__ __forceinline__ void mlp_deltas_warp(BwdSmem &sm, int warp, int lane)
             const int col = nt * 8 + 2 * t;
             const float2 e0 = relu_mask(&sm.h1[r0 * kHStride + col], c[nt][0], c[nt][1]);
             const float2 e1 = relu_mask(&sm.h1[r1 * kHStride + col], c[nt][2], c[nt][3]);
-            *reinterpret_cast<float2 *>(&sm.d1[r0 * kDS + col]) = e0;
-            *reinterpret_cast<float2 *>(&sm.d1[r1 * kDS + col]) = e1;
+            *reinterpret_cast<float2 *>(&sm.dd[r0 * kDS + col]) = e0;
+            *reinterpret_cast<float2 *>(&sm.dd[r1 * kDS + col]) = e1;
             const uint32_t a0 = to_tf32(e0.x), a1 = to_tf32(e1.x), a2 = to_tf32(e0.y),
                            a3 = to_tf32(e1.y);
 #pragma unroll
@@ -334,36 +351,40 @@ __device__ __forceinline__ void mlp_deltas_warp(BwdSmem &sm, int warp, int lane)
     }
 }
 
-// Adds the weight gradients of the CTA's 128 rows to this lane's
-// accumulators: dW2 = d2^T [h1 | 1], dW1 = d1^T [x | 1], dW3^T = h2^T d3,
-// each a sum over the rows (the K dimension), warp w taking output rows
+// Weight gradients of the CTA's 128 rows into this lane's accumulators, each
+// a sum over the rows (the K dimension), warp w taking output rows
 // 16w..16w+15.
-__device__ __forceinline__ void mlp_wgrad_cta(const BwdSmem &sm, int warp, int lane, WGradAcc &acc) {
+__device__ __forceinline__ void mlp_wgrad2_cta(const BwdSmem &sm, int warp, int lane, WGradAcc &acc) {
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = warp * 16 + g, m1 = m0 + 8;
+#pragma unroll 2
+    for (int ks = 0; ks < kRows / 8; ++ks) {
+        const int ra = ks * 8 + t, rb = ra + 4;
+        const uint32_t a0 = to_tf32(sm.dd[ra * kDS + m0]), a1 = to_tf32(sm.dd[ra * kDS + m1]);
+        const uint32_t a2 = to_tf32(sm.dd[rb * kDS + m0]), a3 = to_tf32(sm.dd[rb * kDS + m1]);
+#pragma unroll
+        for (int nt = 0; nt < 9; ++nt)
+            mma_tf32(acc.w2[nt], a0, a1, a2, a3, bf_tf32(&sm.h1[ra * kHStride + nt * 8 + g]),
+                     bf_tf32(&sm.h1[rb * kHStride + nt * 8 + g]));
+        mma_tf32(acc.w3, bf_tf32(&sm.h2[ra * kHStride + m0]), bf_tf32(&sm.h2[ra * kHStride + m1]),
+                 bf_tf32(&sm.h2[rb * kHStride + m0]), bf_tf32(&sm.h2[rb * kHStride + m1]),
+                 to_tf32(sm.d3[ra * kD3S + g]), to_tf32(sm.d3[rb * kD3S + g]));
+    }
+}
+
+__device__ __forceinline__ void mlp_wgrad1_cta(const BwdSmem &sm, int warp, int lane, WGradAcc &acc) {
     const int g = lane >> 2, t = lane & 3;
     const int m0 = warp * 16 + g, m1 = m0 + 8;
     const __nv_bfloat16 *X = &sm.mlp.x[0][0];
 #pragma unroll 2
     for (int ks = 0; ks < kRows / 8; ++ks) {
         const int ra = ks * 8 + t, rb = ra + 4;
-        {
-            const uint32_t a0 = to_tf32(sm.d2[ra * kDS + m0]), a1 = to_tf32(sm.d2[ra * kDS + m1]);
-            const uint32_t a2 = to_tf32(sm.d2[rb * kDS + m0]), a3 = to_tf32(sm.d2[rb * kDS + m1]);
+        const uint32_t a0 = to_tf32(sm.dd[ra * kDS + m0]), a1 = to_tf32(sm.dd[ra * kDS + m1]);
+        const uint32_t a2 = to_tf32(sm.dd[rb * kDS + m0]), a3 = to_tf32(sm.dd[rb * kDS + m1]);
 #pragma unroll
-            for (int nt = 0; nt < 9; ++nt)
-                mma_tf32(acc.w2[nt], a0, a1, a2, a3, bf_tf32(&sm.h1[ra * kHStride + nt * 8 + g]),
-                         bf_tf32(&sm.h1[rb * kHStride + nt * 8 + g]));
-        }
-        {
-            const uint32_t a0 = to_tf32(sm.d1[ra * kDS + m0]), a1 = to_tf32(sm.d1[ra * kDS + m1]);
-            const uint32_t a2 = to_tf32(sm.d1[rb * kDS + m0]), a3 = to_tf32(sm.d1[rb * kDS + m1]);
-#pragma unroll
-            for (int ft = 0; ft < 3; ++ft)
-                mma_tf32(acc.w1[ft], a0, a1, a2, a3, bf_tf32(&X[ra * kXStride + ft * 8 + g]),
-                         bf_tf32(&X[rb * kXStride + ft * 8 + g]));
-        }
-        mma_tf32(acc.w3, bf_tf32(&sm.h2[ra * kHStride + m0]), bf_tf32(&sm.h2[ra * kHStride + m1]),
-                 bf_tf32(&sm.h2[rb * kHStride + m0]), bf_tf32(&sm.h2[rb * kHStride + m1]),
-                 to_tf32(sm.d3[ra * kD3S + g]), to_tf32(sm.d3[rb * kD3S + g]));
+        for (int ft = 0; ft < 3; ++ft)
+            mma_tf32(acc.w1[ft], a0, a1, a2, a3, bf_tf32(&X[ra * kXStride + ft * 8 + g]),
+                     bf_tf32(&X[rb * kXStride + ft * 8 + g]));
     }
 }
 
@@ -628,9 +649,13 @@ __global__ void __launch_bounds__(kMlpThreads) k_preprocess_bwd(RenderArgs args,
 #pragma unroll
             for (int k = 0; k < kMlpOut; ++k) sb3[k] += d3[k];
             __syncwarp();
-            mlp_deltas_warp(sm, warp, lane);
+            mlp_d2_warp(sm, warp, lane);
             __syncthreads();
-            mlp_wgrad_cta(sm, warp, lane, wacc);
+            mlp_wgrad2_cta(sm, warp, lane, wacc);
+            __syncthreads();
+            mlp_d1_warp(sm, warp, lane);
+            __syncthreads();
+            mlp_wgrad1_cta(sm, warp, lane, wacc);
             float dx[kDxS];
 #pragma unroll
             for (int k = 0; k < kDxS; k += 4) {
