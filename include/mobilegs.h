@@ -338,9 +338,11 @@ double mgs_now(void);
  *   attrs:     device pointer, n x 24 records (same layout as mgs_scene_desc),
  *              16-byte aligned; precision MGS_PREC_FP32 or MGS_PREC_FP16.
  *   out_rgb:   device, height x width x 3 FP32, caller-owned.
- *   opts:      use_mlp must be 0 (plain mode: phi = 1, stored opacity).
- * Scratch lives in one fixed __device__ array (about 27 MiB) that every GPU
- * loading this library holds until the process exits.  Limits: n <= 131072,
+ *   opts:      use_mlp must be 0 (plain mode: phi = 1, stored opacity);
+ *              flags may hold only MGS_FLAG_NO_CULL and MGS_FLAG_RASTER_FMA
+ *              (any other flag, e.g. MGS_FLAG_SORTED, is MGS_ERR_INVALID_ARG).
+ * Scratch lives in one fixed __device__ array (30,557,440 bytes, about
+ * 29 MiB) that every GPU loading this library holds until the process exits.  Limits: n <= 131072,
  * at most 8192 tiles of 16x16 pixels (1920x1080 fits), at most 4,194,304
  * (tile, Gaussian) pairs; larger n or images are rejected with
  * MGS_ERR_INVALID_ARG before any work, too many pairs with MGS_ERR_OVERFLOW

@@ -150,13 +150,74 @@ def _ptr(t) -> int | None:
     return t.ctypes.data
 
 
-def _stream(stream) -> int | None:
+def _stream(stream, device=None) -> int | None:
     if stream is None:
         import torch
-        return torch.cuda.current_stream().cuda_stream
+        return torch.cuda.current_stream(device).cuda_stream
     if hasattr(stream, "cuda_stream"):
         return stream.cuda_stream
     return int(stream)
+
+
+# CUDA device of every context, workspace and loaded scene created through
+# this module (keyed by handle value), and each scene's Gaussian count, so
+# that output buffers can be checked before the library writes through them.
+_ctx_dev: dict = {}
+_ws_dev: dict = {}
+_scene_info: dict = {}
+
+
+def _dev_of(handle, table, what):
+    v = getattr(handle, "value", handle)
+    if v not in table:
+        raise ValueError(f"unknown {what} handle (not created through this module)")
+    return table[v]
+
+
+def _check_dev_tensor(t, shape, dtype, device, what, optional=False):
+    """Raise ValueError unless t is a contiguous CUDA tensor of `shape` and
+    `dtype` on CUDA device `device` (None allowed when optional)."""
+    import torch
+    if t is None:
+        if optional:
+            return
+        raise ValueError(f"{what} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{what} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{what} is on cuda:{t.device.index}, the call runs on cuda:{device}")
+
+
+def _check_host_buffer(t, shape, what):
+    """Raise ValueError unless t is a contiguous float32 host buffer (CPU
+    tensor or numpy array) of `shape`."""
+    import torch
+    if isinstance(t, torch.Tensor):
+        ok = (not t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+              and tuple(t.shape) == tuple(shape))
+    else:
+        ok = (isinstance(t, np.ndarray) and t.dtype == np.float32 and t.flags.c_contiguous
+              and tuple(t.shape) == tuple(shape))
+    if not ok:
+        raise ValueError(f"{what} must be a contiguous float32 host buffer of shape {tuple(shape)}")
+
+
+def _check_render_outputs(ws, cam, out_rgb, out_aux=None, out_count=None, out_depth=None,
+                          rgb_optional=False):
+    import torch
+    dev = _dev_of(ws, _ws_dev, "workspace")
+    H, W = int(cam.height), int(cam.width)
+    _check_dev_tensor(out_rgb, (H, W, 3), torch.float32, dev, "out_rgb", rgb_optional)
+    _check_dev_tensor(out_aux, (5, H, W), torch.float32, dev, "out_aux", True)
+    _check_dev_tensor(out_count, (H, W), torch.int32, dev, "out_count", True)
+    _check_dev_tensor(out_depth, (H, W), torch.float32, dev, "out_depth", True)
+    return dev
 
 
 def camera_struct(cam) -> mgs_camera:
@@ -188,11 +249,13 @@ def render_opts(use_mlp=False, rgb_residual=False, bg=(0.0, 0.0, 0.0), flags=0) 
 def mgs_ctx_create(device: int = 0):
     h = ctypes.c_void_p()
     _check(lib().mgs_ctx_create(device, ctypes.byref(h)))
+    _ctx_dev[h.value] = int(device)
     return h
 
 
 def mgs_ctx_destroy(ctx):
     _check(lib().mgs_ctx_destroy(ctx))
+    _ctx_dev.pop(getattr(ctx, "value", ctx), None)
 
 
 def mgs_ctx_info(ctx):
@@ -240,13 +303,18 @@ def mgs_load_scene(ctx, attrs, mlp=None, stream=None, order=MGS_ORDER_AUTO):
             d.mlp_w4, d.mlp_b4 = arrs[6].ctypes.data, arrs[7].ctypes.data
         keep += arrs
         (d.mlp_w1, d.mlp_b1, d.mlp_w2, d.mlp_b2, d.mlp_w3, d.mlp_b3) = [x.ctypes.data for x in arrs[:6]]
+    dev = _dev_of(ctx, _ctx_dev, "context")
+    if on_dev and a.device.index != dev:
+        raise ValueError(f"attrs is on cuda:{a.device.index}, the context on cuda:{dev}")
     h = ctypes.c_void_p()
-    _check(lib().mgs_load_scene(ctx, ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+    _check(lib().mgs_load_scene(ctx, ctypes.byref(d), _stream(stream, dev), ctypes.byref(h)))
+    _scene_info[h.value] = (dev, d.n)
     return h
 
 
 def mgs_unload_scene(scene):
     _check(lib().mgs_unload_scene(scene))
+    _scene_info.pop(getattr(scene, "value", scene), None)
 
 
 def mgs_scene_bytes(scene) -> int:
@@ -255,12 +323,15 @@ def mgs_scene_bytes(scene) -> int:
 
 def mgs_workspace_create(ctx):
     h = ctypes.c_void_p()
+    dev = _dev_of(ctx, _ctx_dev, "context")
     _check(lib().mgs_workspace_create(ctx, ctypes.byref(h)))
+    _ws_dev[h.value] = dev
     return h
 
 
 def mgs_workspace_destroy(ws):
     _check(lib().mgs_workspace_destroy(ws))
+    _ws_dev.pop(getattr(ws, "value", ws), None)
 
 
 def mgs_workspace_reserve(ws, n, width, height, pairs):
@@ -273,27 +344,36 @@ def mgs_workspace_bytes(ws) -> int:
 
 def mgs_workspace_sync(ws, stream=None, allow_overflow=False):
     pairs = ctypes.c_int64()
-    st = lib().mgs_workspace_sync(ws, _stream(stream), ctypes.byref(pairs))
+    st = lib().mgs_workspace_sync(ws, _stream(stream, _ws_dev.get(getattr(ws, "value", ws))),
+                                  ctypes.byref(pairs))
     _check(st, allow=(MGS_ERR_OVERFLOW,) if allow_overflow else ())
     return st, pairs.value
 
 
 def mgs_render(ws, scene, cam, opts, out_rgb, out_aux=None, out_count=None, stream=None):
+    """out_rgb (H, W, 3) float32, out_aux (5, H, W) float32 and out_count
+    (H, W) int32: contiguous CUDA tensors on the workspace's device (checked
+    here, before the library writes through them)."""
     c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    dev = _check_render_outputs(ws, c, out_rgb, out_aux, out_count)
     _check(lib().mgs_render(ws, scene, ctypes.byref(c), ctypes.byref(opts), _ptr(out_rgb),
-                            _ptr(out_aux), _ptr(out_count), _stream(stream)))
+                            _ptr(out_aux), _ptr(out_count), _stream(stream, dev)))
 
 
 def mgs_render_checked(ws, scene, cam, opts, out_rgb, out_aux=None, out_count=None, stream=None):
     c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    dev = _check_render_outputs(ws, c, out_rgb, out_aux, out_count)
     _check(lib().mgs_render_checked(ws, scene, ctypes.byref(c), ctypes.byref(opts), _ptr(out_rgb),
-                                    _ptr(out_aux), _ptr(out_count), _stream(stream)))
+                                    _ptr(out_aux), _ptr(out_count), _stream(stream, dev)))
 
 
 def mgs_render_depth(ws, scene, cam, opts, out_rgb, out_depth, stream=None):
     c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    if out_depth is None:
+        raise ValueError("out_depth is required")
+    dev = _check_render_outputs(ws, c, out_rgb, out_depth=out_depth)
     _check(lib().mgs_render_depth(ws, scene, ctypes.byref(c), ctypes.byref(opts), _ptr(out_rgb),
-                                  _ptr(out_depth), _stream(stream)))
+                                  _ptr(out_depth), _stream(stream, dev)))
 
 
 def mgs_decode_sh(ctx, h, mlp_d, mlp_v, attrs, stream=None):
@@ -305,6 +385,8 @@ def mgs_decode_sh(ctx, h, mlp_d, mlp_v, attrs, stream=None):
         raise TypeError("h and attrs must both be float16 or float32")
     if not (attrs.is_cuda and h.is_cuda and attrs.is_contiguous() and h.is_contiguous()):
         raise ValueError("h and attrs must be contiguous CUDA tensors")
+    if attrs.device != h.device or attrs.device.index != _dev_of(ctx, _ctx_dev, "context"):
+        raise ValueError("h, attrs and the context must be on the same device")
     if h.shape[1] != 6 or attrs.shape[1] != 24 or h.shape[0] != attrs.shape[0]:
         raise ValueError("h must be (N, 6) and attrs (N, 24)")
     keep, ss = [], []
@@ -316,20 +398,36 @@ def mgs_decode_sh(ctx, h, mlp_d, mlp_v, attrs, stream=None):
         ss.append(mgs_sh_mlp(*[a.ctypes.data for a in arrs]))
     prec = MGS_PREC_FP16 if attrs.dtype == torch.float16 else MGS_PREC_FP32
     _check(lib().mgs_decode_sh(ctx, int(h.shape[0]), prec, _ptr(h), ctypes.byref(ss[0]),
-                               ctypes.byref(ss[1]), _ptr(attrs), _stream(stream)))
+                               ctypes.byref(ss[1]), _ptr(attrs), _stream(stream, attrs.device.index)))
 
 
 def mgs_render_to_host(ws, scene, cam, opts, host_rgb, stream=None):
+    """host_rgb: contiguous float32 host buffer (H, W, 3) (pinned for an
+    asynchronous copy)."""
     c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    dev = _dev_of(ws, _ws_dev, "workspace")
+    _check_host_buffer(host_rgb, (int(c.height), int(c.width), 3), "host_rgb")
     _check(lib().mgs_render_to_host(ws, scene, ctypes.byref(c), ctypes.byref(opts),
-                                    _ptr(host_rgb), _stream(stream)))
+                                    _ptr(host_rgb), _stream(stream, dev)))
 
 
 def mgs_tile_lists(ws, offsets_out=None, gids_out=None, stream=None):
     """(n_tiles, n_pairs) of the workspace's last render; copies the lists
     into the given device tensors when both are passed."""
     n, k = ctypes.c_int64(), ctypes.c_int64()
-    _check(lib().mgs_tile_lists(ws, _stream(stream), ctypes.byref(n), ctypes.byref(k),
+    dev = _dev_of(ws, _ws_dev, "workspace")
+    if offsets_out is not None or gids_out is not None:
+        import torch
+        _check(lib().mgs_tile_lists(ws, _stream(stream, dev), ctypes.byref(n), ctypes.byref(k),
+                                    None, None))
+        _check_dev_tensor(offsets_out, (n.value + 1,), offsets_out.dtype
+                          if offsets_out is not None and offsets_out.dtype in (torch.int32, torch.uint32)
+                          else torch.int32, dev, "offsets_out")
+        if (gids_out is None or not isinstance(gids_out, torch.Tensor) or gids_out.ndim != 1
+                or gids_out.shape[0] < k.value):
+            raise ValueError(f"gids_out must be a 1-D CUDA int32 tensor of at least {k.value} entries")
+        _check_dev_tensor(gids_out, tuple(gids_out.shape), torch.int32, dev, "gids_out")
+    _check(lib().mgs_tile_lists(ws, _stream(stream, dev), ctypes.byref(n), ctypes.byref(k),
                                 _ptr(offsets_out), _ptr(gids_out)))
     return n.value, k.value
 
@@ -342,7 +440,8 @@ def mgs_workspace_stage_times(ws, stream=None):
     """(ms[3], frames): summed (preprocess+MLP, binning, rasterise) times."""
     ms = (ctypes.c_double * 3)()
     fr = ctypes.c_int64()
-    _check(lib().mgs_workspace_stage_times(ws, _stream(stream), ms, ctypes.byref(fr)))
+    _check(lib().mgs_workspace_stage_times(ws, _stream(stream, _dev_of(ws, _ws_dev, "workspace")),
+                                           ms, ctypes.byref(fr)))
     return [ms[0], ms[1], ms[2]], fr.value
 
 
@@ -357,16 +456,29 @@ def mgs_render_static(attrs, cam, opts, out_rgb, stream=None):
     a = attrs.contiguous()
     prec = MGS_PREC_FP16 if a.dtype == torch.float16 else MGS_PREC_FP32
     c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
-    _check(lib().mgs_render_static(_ptr(a), int(a.shape[0]), prec, ctypes.byref(c),
-                                   ctypes.byref(opts), _ptr(out_rgb), _stream(stream)))
+    dev = a.device.index
+    _check_dev_tensor(out_rgb, (int(c.height), int(c.width), 3), torch.float32, dev, "out_rgb")
+    with torch.cuda.device(dev):     # the entry point works on the current device
+        _check(lib().mgs_render_static(_ptr(a), int(a.shape[0]), prec, ctypes.byref(c),
+                                       ctypes.byref(opts), _ptr(out_rgb), _stream(stream, dev)))
 
 
 def mgs_render_backward(ws, scene, cam, opts, dL_drgb, aux, d_attrs, d_mlp=None, stream=None):
     """Adjoint of mgs_render (see include/mobilegs.h); device tensors in/out."""
+    import torch
     c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+    dev = _dev_of(ws, _ws_dev, "workspace")
+    H, W = int(c.height), int(c.width)
+    sdev, n = _dev_of(scene, _scene_info, "scene")
+    if sdev != dev:
+        raise ValueError("scene and workspace are on different devices")
+    _check_dev_tensor(dL_drgb, (H, W, 3), torch.float32, dev, "dL_drgb")
+    _check_dev_tensor(aux, (5, H, W), torch.float32, dev, "aux")
+    _check_dev_tensor(d_attrs, (n, 24), torch.float32, dev, "d_attrs")
+    _check_dev_tensor(d_mlp, (MLP_GRAD_SIZE,), torch.float32, dev, "d_mlp", True)
     _check(lib().mgs_render_backward(ws, scene, ctypes.byref(c), ctypes.byref(opts),
                                      _ptr(dL_drgb), _ptr(aux), _ptr(d_attrs), _ptr(d_mlp),
-                                     _stream(stream)))
+                                     _stream(stream, dev)))
 
 
 def mgs_version() -> str:

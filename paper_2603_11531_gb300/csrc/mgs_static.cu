@@ -39,7 +39,8 @@ constexpr size_t kGidsOff =
     kBasesOff + align256((size_t)bin_scratch_words_for(kMaxBinCtas, kMaxTiles, kMaxGaussians) * sizeof(uint32_t));
 constexpr size_t kWt16Off = kGidsOff + align256(kMaxPairs * sizeof(uint32_t));
 constexpr size_t kStatusOff = kWt16Off + align256(kMaxGaussians * sizeof(uint4));
-constexpr size_t kScratchBytes = kStatusOff + align256(sizeof(DevStatus));  // ~29 MiB
+constexpr size_t kScratchBytes = kStatusOff + align256(sizeof(DevStatus));  // 30,557,440 B
+static_assert(kScratchBytes == 30557440, "the documented size of the static scratch");
 
 // The scratch.  In host code this name is only a host-side stand-in for the
 // device array: its device address comes from cudaGetSymbolAddress.
@@ -99,6 +100,12 @@ extern "C" mgs_status mgs_render_static(const void *attrs, int64_t n, int32_t pr
         return fail_static(MGS_ERR_INVALID_ARG, "image needs more than 8192 tiles (allocation-free limit)");
     if (opts->use_mlp)
         return fail_static(MGS_ERR_INVALID_ARG, "the allocation-free entry point renders without the MLP");
+    // Only flags this entry point honours: the sorted comparator and the MLP
+    // options would silently render something other than what was asked for.
+    if (opts->flags & ~(uint32_t)(MGS_FLAG_NO_CULL | MGS_FLAG_RASTER_FMA))
+        return fail_static(MGS_ERR_INVALID_ARG,
+                           "the allocation-free entry point accepts only MGS_FLAG_NO_CULL and "
+                           "MGS_FLAG_RASTER_FMA");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail_static(MGS_ERR_CUDA, "cudaGetDevice failed");

@@ -7,7 +7,8 @@ from __future__ import annotations
 
 import ctypes
 
-from . import MGS_ERR_TIMEOUT, MGSError, _check, _ptr, camera_struct, lib, mgs_camera
+from . import (MGS_ERR_TIMEOUT, MGSError, _check, _check_dev_tensor, _ctx_dev, _dev_of, _ptr,
+               camera_struct, lib, mgs_camera)
 
 _sig_done = False
 
@@ -54,12 +55,18 @@ class Server:
 
     def __init__(self, ctx, slots: int = 8, max_batch: int = 8, hbm_budget_bytes: int = 8 << 30):
         cfg = mgs_server_config(slots, max_batch, hbm_budget_bytes)
+        self.device = _dev_of(ctx, _ctx_dev, "context")
         h = ctypes.c_void_p()
         _check(_L().mgs_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h
 
     def submit(self, scene, cam, opts, out_rgb) -> int:
+        """out_rgb: contiguous CUDA float32 tensor (H, W, 3) on the server's
+        device; it must stay alive until the ticket completes."""
+        import torch
         c = cam if isinstance(cam, mgs_camera) else camera_struct(cam)
+        _check_dev_tensor(out_rgb, (int(c.height), int(c.width), 3), torch.float32, self.device,
+                          "out_rgb")
         t = ctypes.c_int64()
         _check(_L().mgs_server_submit(self.h, scene, ctypes.byref(c), ctypes.byref(opts),
                                       _ptr(out_rgb), ctypes.byref(t)))

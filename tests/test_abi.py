@@ -65,3 +65,45 @@ def test_no_cpu_fallback_in_package():
     for path in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
         src = open(path).read()
         assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), path
+
+
+def test_binding_rejects_bad_output_buffers_before_any_call(monkeypatch):
+    """A wrong output buffer (host memory, wrong shape, dtype or layout) is a
+    ValueError raised by the binding before the library is called, so the
+    kernels never write through it."""
+    import numpy as np
+    import torch
+
+    import paper_2603_11531_gb300 as m
+    from paper_2603_11531_gb300 import synth
+
+    def no_call():
+        raise AssertionError("the library must not be called")
+
+    monkeypatch.setattr(m, "lib", no_call)
+    ws, scene = object(), object()
+    monkeypatch.setitem(m._ws_dev, id(ws), 0)
+    monkeypatch.setitem(m._scene_info, id(scene), (0, 100))
+    ws_h, sc_h = id(ws), id(scene)
+    cam = synth.look_at((0, 0, -3), (0, 0, 0), 32, 24, 60.0)
+    opts = m.render_opts()
+    bad = [torch.empty((24, 32, 3)),                      # host memory
+           np.empty((24, 32, 3), np.float32),             # numpy (host)
+           None]
+    for out in bad:
+        with pytest.raises(ValueError):
+            m.mgs_render(ws_h, sc_h, cam, opts, out)
+        with pytest.raises(ValueError):
+            m.mgs_render_checked(ws_h, sc_h, cam, opts, out)
+    with pytest.raises(ValueError):
+        m.mgs_render_depth(ws_h, sc_h, cam, opts, torch.empty((24, 32, 3)), None)
+    for host in (np.empty((24, 32), np.float32), np.empty((24, 32, 3), np.float64),
+                 torch.empty((24, 32, 3), dtype=torch.float16),
+                 torch.empty((32, 24, 3)).transpose(0, 1)):
+        with pytest.raises(ValueError):
+            m.mgs_render_to_host(ws_h, sc_h, cam, opts, host)
+    with pytest.raises(ValueError):
+        m.mgs_render_backward(ws_h, sc_h, cam, opts, torch.empty((24, 32, 3)),
+                              torch.empty((5, 24, 32)), torch.empty((100, 24)))
+    with pytest.raises(ValueError):          # handle this module never created
+        m.mgs_render(object(), sc_h, cam, opts, torch.empty((24, 32, 3)))

@@ -542,3 +542,38 @@ def test_predicate_matches_fp64_ellipse_away_from_boundary(oracle_lib):
             n_in += qq <= 9
             n_tot += 1
     assert n_in > 500 and n_tot > 2000
+
+
+def test_tile_lists_are_the_rectangle_set_minus_tiles_without_pixels(oracle_lib):
+    """On a larger unbounded scene: every listed (tile, Gaussian) pair lies in
+    the Gaussian's 3-sigma rectangle (the tile test only removes pairs), and
+    every rectangle pair left out has no pixel centre strictly inside the
+    ellipse q <= 9 (evaluated in FP64 with a 1e-3 margin, so that a pair the
+    FP32 predicate could include is never missing)."""
+    scene = synth.unbounded_scene(20000, seed=9, precision="fp16")
+    cam = synth.orbit_cameras(8, 8.0, 1.0, 320, 213, 60.0)[2]
+    g = oracle.preprocess(scene.attrs, cam)
+    off, gids = oracle.bin_tiles(g, cam.width, cam.height)
+    tx, ty = oracle.tiles(cam.width, cam.height)
+    tile = np.repeat(np.arange(tx * ty), np.diff(off))
+    rect = g["rect"][gids]
+    i, j = tile % tx, tile // tx
+    assert np.all(g["visible"][gids] == 1)
+    assert np.all((rect[:, 0] <= i) & (i < rect[:, 2]) & (rect[:, 1] <= j) & (j < rect[:, 3]))
+    listed = set(zip(tile.tolist(), gids.tolist()))
+    dropped = 0
+    for k in np.flatnonzero(g["visible"]):
+        x0, y0, x1, y1 = g["rect"][k]
+        c = g["conic"][k]
+        m = g["mean"][k]
+        for tj in range(y0, y1):
+            for ti in range(x0, x1):
+                if (tj * tx + ti, int(k)) in listed:
+                    continue
+                dropped += 1
+                px = np.arange(16 * ti, min(16 * ti + 16, cam.width)) + 0.5 - m[0]
+                py = np.arange(16 * tj, min(16 * tj + 16, cam.height)) + 0.5 - m[1]
+                dx, dy = np.meshgrid(px, py)
+                q = c[0] * dx * dx + 2 * c[1] * dx * dy + c[2] * dy * dy
+                assert q.min() > 9.0 - 1e-3, (k, ti, tj)
+    assert dropped > 0 and len(listed) > 0
