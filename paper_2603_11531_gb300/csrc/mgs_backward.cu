@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
     // 16-byte loads hit distinct banks
     __shared__ __align__(16) float red[2][kRedGroup * 10][36];
     const DevCamera &cam = args.cam;
-    const int tile = (int)args.tile_order[blockIdx.x];
+    const int tile = (int)(args.tile_order[blockIdx.x] & kTileMask);
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bx0 = tx * kTile, by0 = ty * kTile + 8 * warp;

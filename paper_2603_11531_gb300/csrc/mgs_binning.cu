@@ -39,7 +39,7 @@ __device__ __forceinline__ void rect_of(const uint2 r, int &x0, int &y0, int &w,
     x0 = r.x & 0xFFFF;
     y0 = r.y & 0xFFFF;
     w = (int)(r.x >> 16) - x0;
-    h = (int)(r.y >> 16) - y0;
+    h = (int)((r.y & ~kRectWide) >> 16) - y0;
 }
 // Number of (tile, Gaussian) pairs of a rectangle.
 __device__ __forceinline__ int rect_pairs(int w, int h) { return w > 0 && h > 0 ? w * h : 0; }
@@ -66,10 +66,10 @@ __device__ __forceinline__ bool tile_may_hit(float mx, float my, float l11, floa
     return __fsub_rn(e1c, h1) <= __fadd_rn(3.0f, m1) && __fsub_rn(e2c, h2) <= __fadd_rn(3.0f, m2);
 }
 
-// Calls f(tile, gid) for the pairs [pa, pb) of the flattened pair numbering
-// of Gaussians [g0, g0 + 32) (one per lane; rectangle after rectangle, row
-// major inside each) whose tile passes tile_may_hit, 32 pairs at a time
-// over the warp's lanes.
+// Calls f(tile, gid, wide) for the pairs [pa, pb) of the flattened pair
+// numbering of Gaussians [g0, g0 + 32) (one per lane; rectangle after
+// rectangle, row major inside each) whose tile passes tile_may_hit, 32 pairs
+// at a time over the warp's lanes; wide = the Gaussian carries kRectWide.
 template <class F>
 __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
                                            const ProjRec *__restrict__ rec, int64_t n, int64_t g0,
@@ -79,8 +79,11 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
     int x0 = 0, y0 = 0, w = 0, h = 0;
     float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
     float gl22 = 0.f;
+    bool wide = false;
     if (i < n) {
-        rect_of(rect[i], x0, y0, w, h);
+        const uint2 r = rect[i];
+        rect_of(r, x0, y0, w, h);
+        wide = (r.y & kRectWide) != 0;
         if (w > 0 && h > 0) {
             ga = rec[i].a;
             gl22 = rec[i].b.x;
@@ -115,6 +118,7 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
         const float l11 = __shfl_sync(0xffffffffu, ga.z, lo);
         const float l21 = __shfl_sync(0xffffffffu, ga.w, lo);
         const float l22 = __shfl_sync(0xffffffffu, gl22, lo);
+        const bool owide = __shfl_sync(0xffffffffu, wide, lo);
         if (p < P) {
             const int k = p - oe;
             // k / ow via the reciprocal, then corrected by one step either way
@@ -123,7 +127,8 @@ __device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
             if (ky * ow > k) --ky;
             else if ((ky + 1) * ow <= k) ++ky;
             const int tx = ox0 + (k - ky * ow), ty = oy0 + ky;
-            if (tile_may_hit(mx, my, l11, l21, l22, tx, ty)) f(ty * tiles_x + tx, (uint32_t)(g0 + lo));
+            if (tile_may_hit(mx, my, l11, l21, l22, tx, ty))
+                f(ty * tiles_x + tx, (uint32_t)(g0 + lo), owide);
         }
     }
 }
@@ -145,7 +150,7 @@ __device__ __forceinline__ int64_t find_group(const unsigned long long *__restri
     return lo;
 }
 
-// Calls f(tile, gid) for the listed pairs of this warp's share of the work
+// Calls f(tile, gid, wide) for the listed pairs of this warp's share of the work
 // plan: group g occupies costs [cexcl[g], cexcl[g + 1]), its visit charge
 // first and then one unit per rectangle pair in the group's pair numbering;
 // warp w of W takes costs [C w / W, C (w + 1) / W) of the total C.
@@ -246,26 +251,39 @@ __global__ void __launch_bounds__(kScanThreads) k_bin_plan(const uint32_t *__res
     if (tid == 0) cexcl[groups] = carry;
 }
 
+// Counts per tile; with `tc` (tensor-core rasteriser) and a frame that has
+// wide Gaussians, also sets kTileWide in tile_count[] of every tile that
+// lists one (per-CTA counts stay below 2^31, so the flag never meets a carry).
 __global__ void __launch_bounds__(kBinThreads, 1) k_bin_count(const uint2 *__restrict__ rect,
                                                            const ProjRec *__restrict__ rec,
                                                            int64_t n, int tiles_x, int T,
                                                            const unsigned long long *__restrict__ excl,
                                                            int64_t groups,
                                                            uint32_t *__restrict__ tile_count,
-                                                           uint32_t *__restrict__ bases) {
+                                                           uint32_t *__restrict__ bases,
+                                                           const DevStatus *__restrict__ status,
+                                                           bool tc) {
     extern __shared__ uint32_t cnt_s[];
+    const bool mark = tc && status->wide_bits != 0u;
     for (int band0 = 0; band0 < T; band0 += kBand) {
         const int bn = min(kBand, T - band0);
         for (int t = threadIdx.x; t < bn; t += blockDim.x) cnt_s[t] = 0u;
         __syncthreads();
-        warp_share_pairs(rect, rec, n, excl, groups, tiles_x, [&](int tile, uint32_t) {
+        warp_share_pairs(rect, rec, n, excl, groups, tiles_x, [&](int tile, uint32_t, bool wide) {
             const int t = tile - band0;
-            if ((unsigned)t < (unsigned)bn) atomicAdd(&cnt_s[t], 1u);
+            if ((unsigned)t < (unsigned)bn) {
+                atomicAdd(&cnt_s[t], 1u);
+                if (mark && wide) atomicOr(&cnt_s[t], kTileWide);
+            }
         });
         __syncthreads();
         for (int t = threadIdx.x; t < bn; t += blockDim.x) {
             const uint32_t v = cnt_s[t];
-            if (v) bases[(int64_t)blockIdx.x * T + band0 + t] = atomicAdd(&tile_count[band0 + t], v);
+            const uint32_t c = v & kTileMask;
+            if (c)
+                bases[(int64_t)blockIdx.x * T + band0 + t] =
+                    atomicAdd(&tile_count[band0 + t], c) & kTileMask;
+            if (v & kTileWide) atomicOr(&tile_count[band0 + t], kTileWide);
         }
         __syncthreads();
     }
@@ -313,7 +331,7 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_scatter(
         for (int t = threadIdx.x; t < bn; t += blockDim.x)
             cur_s[t] = offsets[band0 + t] + bases[(int64_t)blockIdx.x * T + band0 + t];
         __syncthreads();
-        warp_share_pairs(rect, rec, n, excl, groups, tiles_x, [&](int tile, uint32_t gid) {
+        warp_share_pairs(rect, rec, n, excl, groups, tiles_x, [&](int tile, uint32_t gid, bool) {
             const int t = tile - band0;
             if ((unsigned)t < (unsigned)bn) {
                 const uint32_t slot = atomicAdd(&cur_s[t], 1u);
@@ -331,7 +349,9 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_scatter(
 //     floor(log2(length))), so the longest tiles start first and the tail of
 //     the raster launch is made of short tiles;
 //   * hands this frame's weight bound to the rasteriser and resets the
-//     accumulator for the next frame.
+//     accumulator (and the wide-Gaussian flag) for the next frame;
+//   * carries each tile's kTileWide flag from tile_count[] into its order
+//     entry.
 __global__ void __launch_bounds__(kScanThreads) k_scan_order(const uint32_t *__restrict__ count,
                                                              uint32_t *__restrict__ offsets,
                                                              uint32_t *__restrict__ order, int T,
@@ -344,6 +364,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_order(const uint32_t *__r
         carry = 0;
         status->wmax_frame_bits = status->wmax_bits;
         status->wmax_bits = 0u;
+        status->wide_bits = 0u;
     }
     if (tid < 33) hist[tid] = 0u;
     __syncthreads();
@@ -352,7 +373,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_order(const uint32_t *__r
         unsigned long long v[4], local = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            v[k] = (i0 + k < T) ? count[i0 + k] : 0u;
+            v[k] = (i0 + k < T) ? (count[i0 + k] & kTileMask) : 0u;
             local += v[k];
             if (i0 + k < T) {
                 const uint32_t c = (uint32_t)v[k];
@@ -401,8 +422,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_order(const uint32_t *__r
     }
     __syncthreads();
     for (int t = tid; t < T; t += blockDim.x) {
-        const uint32_t c = count[t];
-        order[atomicAdd(&start[c ? 32 - __clz(c) : 0], 1u)] = (uint32_t)t;
+        const uint32_t cw = count[t], c = cw & kTileMask;
+        order[atomicAdd(&start[c ? 32 - __clz(c) : 0], 1u)] = (uint32_t)t | (cw & kTileWide);
     }
 }
 
@@ -451,7 +472,8 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch,
         k_bin_plan<<<1, kScanThreads, plan_smem, stream>>>(grp, groups, excl);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_bin_count<<<C, kBinThreads, smem, stream>>>(a.rect, a.rec, a.n, a.cam.tiles_x, T, excl,
-                                                      groups, a.tile_count, bases);
+                                                      groups, a.tile_count, bases, a.status,
+                                                      tc_raster(a));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_scan_order<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, a.tile_order, T,

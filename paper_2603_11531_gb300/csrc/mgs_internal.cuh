@@ -83,7 +83,11 @@ constexpr unsigned kStatusOverflow = 1u;    // some render exceeded its pair cap
 constexpr unsigned kStatusMmaTimeout = 2u;  // a tcgen05 MMA wait ran out (results invalid)
 struct DevStatus {
     unsigned int overflow;          // kStatus* bits seen since the last sync
-    unsigned int pad;
+    // Nonzero when the current frame has a Gaussian whose weight the FP16
+    // tensor-core sums cannot hold next to the others (kRectWide): set by
+    // preprocessing, read by the count kernel of binning, reset by
+    // k_scan_order.
+    unsigned int wide_bits;
     unsigned long long max_pairs;   // largest pair count seen since the last sync
     unsigned long long last_pairs;  // pair count of the most recent render
     // Largest |w c| and w over the visible Gaussians (FP32 bits; positive
@@ -93,6 +97,21 @@ struct DevStatus {
     unsigned int wmax_bits;
     unsigned int wmax_frame_bits;
 };
+
+// Weight range of the tensor-core sums.  The rasteriser of FP16 scenes sums
+// a w c and a w in FP16 x FP16 products scaled by one power of two per frame
+// (largest weight into [2^14, 2^15)).  Eq. 3 gives w >= 1 for every Gaussian
+// in front of the camera, so weights below kWideWeight keep at least 2^-5
+// after scaling, and their FP16 high + low parts at least 20 bits.  A
+// Gaussian with w * max(1, c) >= kWideWeight (or w < 1, or not finite) is
+// "wide": preprocessing sets kRectWide in its rectangle, binning marks every
+// tile that lists it (kTileWide in the tile's rasterisation-order entry), and
+// those tiles take the FP32 FMA sums instead.  The frame's scale is taken
+// over the other Gaussians only.
+constexpr float kWideWeight = 1048576.0f;   // 2^20
+constexpr unsigned kRectWide = 0x80000000u; // in rect.y (above y_hi << 16)
+constexpr unsigned kTileWide = 0x80000000u; // in tile_order[] and tile_count[]
+constexpr unsigned kTileMask = 0x7FFFFFFFu;
 
 // Projected Gaussian (48 bytes), written by preprocessing, read by the
 // rasteriser:
@@ -118,10 +137,10 @@ struct RenderArgs {
     unsigned flags;
     // workspace
     ProjRec *rec;
-    uint2 *rect;              // packed (x_lo | x_hi << 16, y_lo | y_hi << 16)
+    uint2 *rect;              // packed (x_lo | x_hi << 16, y_lo | y_hi << 16 | kRectWide)
     uint32_t *tile_count;     // [T]
     uint32_t *tile_offsets;   // [T + 1]
-    uint32_t *tile_order;     // [T] rasterisation order (longest lists first)
+    uint32_t *tile_order;     // [T] rasterisation order (longest lists first), | kTileWide
     uint32_t *gids;           // [capacity]
     uint4 *wt16;              // [n] tensor-core weights (FP16 high / low parts), see tc_raster()
     const uint32_t *perm;     // [n] stored position -> caller index (null: identity)

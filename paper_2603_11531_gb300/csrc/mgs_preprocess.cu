@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kWide ? tcw::kThreads : (kTC ? tc::kThreads : 
     camera_centre(cam, cc);
     const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f;
     float wbound = 0.0f;
+    bool any_wide = false;
 
     for (int64_t base = (int64_t)blockIdx.x * kStep; base < args.n;
          base += (int64_t)gridDim.x * kStep) {
@@ -293,15 +294,23 @@ __global__ void __launch_bounds__(kWide ? tcw::kThreads : (kTC ? tc::kThreads : 
         r.b = make_float4(c.l22, __log2f(opa), -w, -w * rgb[0]);
         r.c = make_float4(-w * rgb[1], -w * rgb[2], c.tz, -w * c.tz);
         args.rec[i] = r;
+        // weights outside the range of the FP16 tensor-core sums
+        const float wm = w * fmaxf(fmaxf(1.0f, rgb[0]), fmaxf(rgb[1], rgb[2]));
+        const bool wide = !(w >= 1.0f && wm < kWideWeight);
         args.rect[i] = make_uint2((unsigned)c.rect[0] | ((unsigned)c.rect[2] << 16),
-                                  (unsigned)c.rect[1] | ((unsigned)c.rect[3] << 16));
-        wbound = fmaxf(wbound, w * fmaxf(fmaxf(1.0f, rgb[0]), fmaxf(rgb[1], rgb[2])));
+                                  (unsigned)c.rect[1] | ((unsigned)c.rect[3] << 16) |
+                                      (wide ? kRectWide : 0u));
+        if (wide) any_wide = true;
+        else wbound = fmaxf(wbound, wm);
     }
-    // bound on the rasteriser's weights |w|, |w c| for this frame
+    // bound on the rasteriser's weights |w|, |w c| for this frame (Gaussians
+    // that are not wide)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wbound = fmaxf(wbound, __shfl_xor_sync(0xffffffffu, wbound, o));
     if ((threadIdx.x & 31) == 0 && wbound > 0.0f)
         atomicMax(&args.status->wmax_bits, __float_as_uint(wbound));
+    if (__any_sync(0xffffffffu, any_wide) && (threadIdx.x & 31) == 0)
+        atomicOr(&args.status->wide_bits, 1u);
     if constexpr (kWide) {
         tcw::teardown(smem_raw, wl);
         if (!tc_ok && threadIdx.x == 0) atomicOr(&args.status->overflow, kStatusMmaTimeout);

@@ -228,7 +228,8 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
 // column c + 4 is the sum with a 22-bit weight; binning prepares these FP16
 // weights once per Gaussian (k_bin_scatter), scaled by a power of two when
 // the frame's largest weight would overflow FP16 (the scale cancels in A / B
-// and is divided out here).  T stays in FP32 FMAs.
+// and is divided out here).  T stays in FP32 FMAs.  Tiles listing a Gaussian
+// outside that scale's range (kTileWide) are rasterised by the FMA tile code.
 constexpr int kTcThreads = 128;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kChunk = 8;        // candidates per MMA (K)
@@ -518,14 +519,26 @@ template <bool kAux, bool kCount, bool kDepth = false>
 __global__ void __launch_bounds__(kThreads) k_raster(RenderArgs args) {
     __shared__ ulonglong2 buf[kWarps][kDepth ? 6 : 5][32];
     if (args.status->last_pairs > args.capacity) return;  // overflowed: lists incomplete
-    raster_tile<kAux, kCount, kDepth>(args, (int)args.tile_order[blockIdx.x], buf);
+    raster_tile<kAux, kCount, kDepth>(args, (int)(args.tile_order[blockIdx.x] & kTileMask), buf);
 }
 
+// Tiles that list a Gaussian whose weight the FP16 sums cannot hold next to
+// the others (kTileWide, see kWideWeight) take the FP32 FMA tile code on the
+// CTA's first two warps.
 template <bool kAux, bool kCount, bool kDepth = false>
 __global__ void __launch_bounds__(kTcThreads) k_raster_tc(RenderArgs args) {
-    __shared__ TcSmem sm;
+    __shared__ union {
+        TcSmem tc;
+        ulonglong2 buf[kWarps][kDepth ? 6 : 5][32];
+    } sm;
     if (args.status->last_pairs > args.capacity) return;  // overflowed: lists incomplete
-    raster_tile_tc<kAux, kCount, kDepth>(args, (int)args.tile_order[blockIdx.x], sm);
+    const uint32_t ord = args.tile_order[blockIdx.x];
+    const int tile = (int)(ord & kTileMask);
+    if (ord & kTileWide) {
+        if (threadIdx.x < kThreads) raster_tile<kAux, kCount, kDepth>(args, tile, sm.buf);
+    } else {
+        raster_tile_tc<kAux, kCount, kDepth>(args, tile, sm.tc);
+    }
 }
 
 // Persistent, batched: the tiles of several views (different scenes and
@@ -533,7 +546,7 @@ __global__ void __launch_bounds__(kTcThreads) k_raster_tc(RenderArgs args) {
 // an atomic counter until the list is exhausted.  Items are numbered view by
 // view (prefix[v] = first item of view v), each view's tiles longest first.
 // A CTA has four warps: FP16 views use all four (tensor-core sums), FP32
-// views the first two (FMA sums).
+// views and wide tiles (kTileWide) the first two (FMA sums).
 __global__ void __launch_bounds__(kTcThreads) k_raster_batch(const RenderArgs *__restrict__ views,
                                                              const int *__restrict__ prefix,
                                                              int nviews,
@@ -557,8 +570,9 @@ __global__ void __launch_bounds__(kTcThreads) k_raster_batch(const RenderArgs *_
         }
         const RenderArgs &a = views[lo];
         if (a.status->last_pairs > a.capacity) continue;   // that view overflowed
-        const int tile = (int)a.tile_order[item - prefix[lo]];
-        if (use_tc(a))
+        const uint32_t ord = a.tile_order[item - prefix[lo]];
+        const int tile = (int)(ord & kTileMask);
+        if (use_tc(a) && !(ord & kTileWide))
             raster_tile_tc<false, false>(a, tile, sm.tc);
         else if (threadIdx.x < kThreads)
             raster_tile<false, false>(a, tile, sm.buf);

@@ -230,7 +230,7 @@ template <bool kCount>
 __global__ void __launch_bounds__(64) k_raster_sorted(RenderArgs args, const uint32_t *__restrict__ sorted) {
     __shared__ float4 buf[2][3][32];
     const DevCamera &cam = args.cam;
-    const int tile = (int)args.tile_order[blockIdx.x];
+    const int tile = (int)(args.tile_order[blockIdx.x] & kTileMask);
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bx0 = tx * kTile, by0 = ty * kTile + 8 * warp;

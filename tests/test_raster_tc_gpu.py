@@ -13,7 +13,10 @@ Bars:
     of the colours involved (< 2 here);
   * chunk edges: lists shorter than, equal to and longer than one chunk of
     16, empty tiles and a ragged image;
-  * weights beyond the FP16 range are scaled by a power of two.
+  * weights beyond the FP16 range are scaled by a power of two;
+  * a Gaussian whose weight the FP16 sums cannot hold next to the others
+    (Eq. 3's exp(s_max / d) is unbounded) sends the tiles that list it to
+    the FP32 FMA sums, and every other pixel keeps its tensor-core sums.
 """
 import numpy as np
 import pytest
@@ -120,3 +123,38 @@ def test_tc_culling_is_exact(R):
         R.unload_scene(h)
     assert bool((a["count"] == b["count"]).all())
     assert float((a["rgb"] - b["rgb"]).abs().max()) <= 1e-5
+
+
+@pytest.mark.parametrize("x_off", [0.0, 0.02])
+def test_tc_weight_span_beyond_fp16_range(R, x_off):
+    """Ordinary Gaussians (w about 3) beside one needle with s_max = 8 at view
+    depth 0.25, so w = exp(32) > 2^46: one per-frame FP16 scale cannot hold
+    both (the ordinary weights would fall below FP16's smallest subnormal).
+    On the optical axis the needle covers about 30 pixels across the corner
+    of four tiles; 0.02 off axis it smears into a band across the image.
+    Every pixel -- those the needle covers, those of its tiles it does not
+    cover, and all others -- stays within the FP16-scene bar of the oracle;
+    the depth image (Eq. 5) too."""
+    base = synth.uniform_scene(3000, seed=71).attrs
+    big = np.zeros((1, 24), np.float32)
+    big[0, 0:3] = (x_off, 0.0, -2.75)
+    big[0, 3:6] = (0.002, 0.002, 8.0)
+    big[0, 6] = 1.0
+    big[0, 10] = 0.9
+    big[0, 11:14] = (np.array([0.9, 0.2, 0.1]) - 0.5) / SH_C0
+    scene = synth.Scene(np.concatenate([base, big]).astype(np.float16))
+    cam = synth.look_at((0, 0, -3), (0, 0, 0), 96, 64, 60.0)
+    g = oracle.preprocess(scene.attrs, cam)
+    assert g["weight"][-1] > 2.0 ** 40 and g["visible"][-1] == 1
+    tc, fma = _both(R, scene, cam, bg=(0.1, 0.2, 0.3))
+    ref = oracle.render(scene.attrs, cam, bg=(0.1, 0.2, 0.3), want_count=True)
+    covered = np.array([[oracle.includes(g[-1], x, y) for x in range(96)] for y in range(64)])
+    assert covered.any() and (~covered).any()
+    _check(tc, fma, ref)
+    h = R.load_scene(scene)
+    try:
+        d = R.render_depth(h, cam)["depth"].cpu().numpy()
+    finally:
+        R.unload_scene(h)
+    dref = oracle.render_depth(scene.attrs, cam)["depth"]
+    assert np.abs(d - dref).max() <= 2e-3 * dref.max()
