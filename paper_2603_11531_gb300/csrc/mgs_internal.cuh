@@ -165,20 +165,31 @@ __host__ __device__ inline bool tc_raster(const RenderArgs &a) {
 }
 
 // Can Gaussian (m, l) include any pixel centre of the block centred at (bx, by)
-// with half extents (hx, hy)?  Sound for the exact FP32 test: the slab bounds
-// |e1| <= 3 and |e2| <= 3 hold for every included pixel, and the margin
-// (2^-18 relative) covers the rounding of both evaluations.
+// with half extents (hx, hy)?  In the whitened coordinates e1 = l11 dx +
+// l21 dy, e2 = l22 dy an included pixel lies in the disc e1^2 + e2^2 <= 9, so
+// inside the octagon |e1|, |e2| <= 3 and |e1 +- e2| <= 3 sqrt(2); the block
+// maps to a parallelogram, and each of the four slab tests compares the
+// block centre's coordinate with the parallelogram's half extent along it.
+// Sound for the exact FP32 test: the margin (2^-18 relative, twice that for
+// the diagonal slabs) covers the rounding of the test and of the FP32
+// predicate.  The diagonal slabs remove about 14% of the (block, Gaussian)
+// candidates that the axis slabs alone keep.
 __device__ __forceinline__ bool block_may_hit(float mx, float my, float l11, float l21, float l22,
                                               float bx, float by, float hx, float hy) {
     const float dxb = bx - mx, dyb = by - my;
-    const float e1c = fabsf(fmaf(l11, dxb, l21 * dyb));
-    const float h1 = fmaf(fabsf(l11), hx, fabsf(l21) * hy);
-    const float m1 = 3.814697265625e-06f *
-                     (fabsf(l11) * (fabsf(dxb) + hx) + fabsf(l21) * (fabsf(dyb) + hy) + 4.0f);
-    const float e2c = fabsf(l22 * dyb);
-    const float h2 = fabsf(l22) * hy;
-    const float m2 = 3.814697265625e-06f * (fabsf(l22) * (fabsf(dyb) + hy) + 4.0f);
-    return (e1c - h1 <= 3.0f + m1) && (e2c - h2 <= 3.0f + m2);
+    const float e1 = fmaf(l11, dxb, l21 * dyb);
+    const float e2 = l22 * dyb;
+    const float a11 = fabsf(l11), a21 = fabsf(l21), a22 = fabsf(l22);
+    const float m = 3.814697265625e-06f *
+                    fmaf(a11, fabsf(dxb) + hx, fmaf(a21 + a22, fabsf(dyb) + hy, 4.0f));
+    const float xh = a11 * hx;
+    const float h1 = fmaf(a21, hy, xh);
+    const float h2 = a22 * hy;
+    const float hu = fmaf(fabsf(l21 + l22), hy, xh);
+    const float hv = fmaf(fabsf(l21 - l22), hy, xh);
+    const float r2 = 4.2426410f + 2.0f * m;   // 3 sqrt(2), rounded up
+    return (fabsf(e1) - h1 <= 3.0f + m) && (fabsf(e2) - h2 <= 3.0f + m) &&
+           (fabsf(e1 + e2) - hu <= r2) && (fabsf(e1 - e2) - hv <= r2);
 }
 
 // Scratch of the sorted comparator (mgs_sorted.cu).

@@ -233,7 +233,7 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
 constexpr int kTcThreads = 128;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kChunk = 8;        // candidates per MMA (K)
-constexpr int kRing = 40;        // candidate slots per warp: five chunks
+constexpr int kRing = 64;        // candidate slots per warp: eight chunks (a power of two)
 
 // Ring slot s stores its geometry in pair-interleaved words, so that lane t
 // reads the two entries 2t, 2t + 1 of a chunk with one 16-byte load each:
@@ -383,7 +383,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
         bool clamp = false;
         int pos = 0;
         if (cand) {
-            pos = (head + count + __popc(bal & ((1u << lane) - 1u))) % kRing;
+            pos = (head + count + __popc(bal & ((1u << lane) - 1u))) & (kRing - 1);
             float *q = reinterpret_cast<float *>(&geo[0][pos >> 1]);
             const int o = pos & 1;
             q[o] = a.x;
@@ -415,7 +415,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             else
                 tc_chunk<kCount, false, kDepth>(geo, wt, head, g, t, pxc, pyc, kq2, T, D, cnt, wd, AD);
             clamp_mask &= ~(0xFFull << head);
-            head = head + kChunk == kRing ? 0 : head + kChunk;
+            head = (head + kChunk) & (kRing - 1);
             count -= kChunk;
         }
         __syncwarp();
@@ -423,7 +423,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     if (count > 0) {
         // pad the last chunk with entries that include no pixel and weigh 0
         if (lane < kChunk - count) {
-            const int pos = (head + count + lane) % kRing;
+            const int pos = (head + count + lane) & (kRing - 1);
             const int o = pos & 1;
             float *q = reinterpret_cast<float *>(&geo[0][pos >> 1]);
             q[o] = 1e30f;
