@@ -182,13 +182,16 @@ mgs_status mgs_workspace_sync(mgs_workspace ws, mgs_stream stream,
 
 /* Per-stage device timing (the runtime breakdown the paper reports in
  * Fig. 2 and Fig. 6).  While enabled, every render on the workspace records
- * CUDA events on its stream around (0) preprocessing incl. the MLP,
- * (1) binning (count reset, scan, scatter) and (2) rasterisation. */
+ * CUDA events on its stream around (0) preprocessing incl. the MLP, the four
+ * parts of binning -- (1) the work plan (count reset, pair counts per group,
+ * plan scan), (2) the tile count, (3) the tile scan and rasterisation order,
+ * (4) the scatter of the lists -- and (5) rasterisation (the sorted
+ * comparator's sort and blend; the backward pass's adjoint). */
 mgs_status mgs_workspace_set_timing(mgs_workspace ws, int32_t enable);
-/* Wait for `stream`; ms[0..2] = summed stage times in milliseconds of the
+/* Wait for `stream`; ms[0..5] = summed stage times in milliseconds of the
  * renders timed since the previous call, *frames = their number.  Resets. */
 mgs_status mgs_workspace_stage_times(mgs_workspace ws, mgs_stream stream,
-                                     double ms[3], int64_t *frames);
+                                     double ms[6], int64_t *frames);
 
 /* ---- rendering (Sec. 3.1, Eq. 2-4) --------------------------------------- */
 
@@ -264,6 +267,14 @@ mgs_status mgs_render_to_host(mgs_workspace ws, mgs_scene scene,
 mgs_status mgs_tile_lists(mgs_workspace ws, mgs_stream stream, int64_t *n_tiles,
                           int64_t *n_pairs, uint32_t *offsets_out,
                           uint32_t *gids_out);
+
+/* Facts of the workspace's most recent render, for measurement: Gaussians
+ * that passed culling (visible), listed (tile, Gaussian) pairs, and tiles
+ * whose A, B sums ran in FP32 because they list a Gaussian whose Eq. 3 weight
+ * the FP16 tensor-core sums cannot hold next to the others.  Waits for
+ * `stream`.  MGS_ERR_INVALID_ARG before the first render. */
+mgs_status mgs_frame_stats(mgs_workspace ws, mgs_stream stream, int64_t *visible,
+                           int64_t *pairs, int64_t *fp32_sum_tiles);
 
 /* ---- differentiation (adjoint of Sec. 3.1 Eq. 2-4, Sec. 3.2, App. B) ------- */
 
@@ -356,6 +367,16 @@ mgs_status mgs_render_static(const void *attrs, int64_t n, int32_t precision,
                              float *out_rgb, mgs_stream stream);
 
 /* ---- diagnostics --------------------------------------------------------- */
+
+/* Measured issue rates of the two pipes that bound the rasteriser (Sec. 3.1,
+ * Eq. 2: one exponential and about 16 FP32 operations per included
+ * pixel-Gaussian pair), per SM per clock cycle on CUDA device `device`:
+ * ex2.approx.ftz.f32 (MUFU) and FP32 FFMA.  Blocks of 256 threads run eight
+ * independent dependency chains per thread and record their SM and first and
+ * last cycle on its counter; per SM, operations over the span of its blocks,
+ * averaged over the SMs.  Synchronous; allocates and frees two small device
+ * buffers.  MGS_ERR_INVALID_ARG for NULL outputs or a bad device. */
+mgs_status mgs_probe_rates(int32_t device, double *ex2_per_sm_clk, double *ffma_per_sm_clk);
 
 const char *mgs_last_error(void);
 const char *mgs_version(void);

@@ -46,7 +46,7 @@ EXPORTS = (
     "mgs_version", "mgs_workspace_set_timing", "mgs_workspace_stage_times",
     "mgs_render_static", "mgs_render_backward", "mgs_render_depth", "mgs_decode_sh",
     "mgs_server_create", "mgs_server_destroy", "mgs_server_submit", "mgs_server_wait",
-    "mgs_server_ticket", "mgs_server_stats", "mgs_now",
+    "mgs_server_ticket", "mgs_server_stats", "mgs_now", "mgs_probe_rates", "mgs_frame_stats",
 )
 MLP_GRAD_SIZE = 5957
 
@@ -117,6 +117,8 @@ def lib():
                 "mgs_render_depth": ([P, P, ctypes.POINTER(mgs_camera),
                                       ctypes.POINTER(mgs_render_opts), P, P, P], I32),
                 "mgs_tile_lists": ([P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P], I32),
+                "mgs_frame_stats": ([P, P, ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                     ctypes.POINTER(I64)], I32),
                 "mgs_workspace_set_timing": ([P, I32], I32),
                 "mgs_workspace_stage_times": ([P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], I32),
                 "mgs_render_static": ([P, I64, I32, ctypes.POINTER(mgs_camera),
@@ -125,6 +127,8 @@ def lib():
                                          ctypes.POINTER(mgs_render_opts), P, P, P, P, P], I32),
                 "mgs_decode_sh": ([P, I64, I32, P, ctypes.POINTER(mgs_sh_mlp),
                                    ctypes.POINTER(mgs_sh_mlp), P, P], I32),
+                "mgs_probe_rates": ([I32, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)], I32),
                 "mgs_last_error": ([], ctypes.c_char_p),
                 "mgs_version": ([], ctypes.c_char_p),
             }
@@ -432,17 +436,26 @@ def mgs_tile_lists(ws, offsets_out=None, gids_out=None, stream=None):
     return n.value, k.value
 
 
+def mgs_frame_stats(ws, stream=None) -> dict:
+    """Visible Gaussians, listed pairs and FP32-sum tiles of the last render."""
+    v, k, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().mgs_frame_stats(ws, _stream(stream, _dev_of(ws, _ws_dev, "workspace")),
+                                 ctypes.byref(v), ctypes.byref(k), ctypes.byref(t)))
+    return {"visible": v.value, "pairs": k.value, "wide_tiles": t.value}
+
+
 def mgs_workspace_set_timing(ws, enable: bool):
     _check(lib().mgs_workspace_set_timing(ws, int(bool(enable))))
 
 
 def mgs_workspace_stage_times(ws, stream=None):
-    """(ms[3], frames): summed (preprocess+MLP, binning, rasterise) times."""
-    ms = (ctypes.c_double * 3)()
+    """(ms[6], frames): summed times of preprocess+MLP, binning plan, tile
+    count, tile scan, list scatter and rasterise."""
+    ms = (ctypes.c_double * 6)()
     fr = ctypes.c_int64()
     _check(lib().mgs_workspace_stage_times(ws, _stream(stream, _dev_of(ws, _ws_dev, "workspace")),
                                            ms, ctypes.byref(fr)))
-    return [ms[0], ms[1], ms[2]], fr.value
+    return [ms[k] for k in range(6)], fr.value
 
 
 def mgs_render_static(attrs, cam, opts, out_rgb, stream=None):
@@ -479,6 +492,13 @@ def mgs_render_backward(ws, scene, cam, opts, dL_drgb, aux, d_attrs, d_mlp=None,
     _check(lib().mgs_render_backward(ws, scene, ctypes.byref(c), ctypes.byref(opts),
                                      _ptr(dL_drgb), _ptr(aux), _ptr(d_attrs), _ptr(d_mlp),
                                      _stream(stream, dev)))
+
+
+def mgs_probe_rates(device: int = 0):
+    """(ex2 per SM per clock, FP32 FFMA per SM per clock), measured."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mgs_probe_rates(int(device), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def mgs_version() -> str:

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libmobilegs.so")
 
 SOURCES = ["mgs_api.cu", "mgs_preprocess.cu", "mgs_binning.cu", "mgs_raster.cu", "mgs_static.cu",
            "mgs_backward.cu", "mgs_server.cu",
-           "mgs_sorted.cu", "mgs_sh_decode.cu", "mgs_order.cu"]
+           "mgs_sorted.cu", "mgs_sh_decode.cu", "mgs_order.cu", "mgs_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
               "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]

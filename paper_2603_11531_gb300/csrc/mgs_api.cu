@@ -82,6 +82,10 @@ struct mgs_scene_s {
     int64_t bytes = 0;
 };
 
+// Events per timed render: start, after preprocessing, after the binning plan,
+// after the count, after the tile scan, after the scatter, after the raster.
+constexpr int kStageEvents = 7;
+
 struct mgs_workspace_s {
     mgs_ctx ctx = nullptr;
     int64_t n_cap = 0;
@@ -110,7 +114,7 @@ struct mgs_workspace_s {
     uint64_t grow_hint = 0;  // pairs needed by an overflowed render
     bool timing = false;
     std::vector<cudaEvent_t> event_pool;
-    std::vector<std::array<cudaEvent_t, 4>> pending;  // per timed render
+    std::vector<std::array<cudaEvent_t, kStageEvents>> pending;  // per timed render
 };
 
 namespace {
@@ -271,7 +275,7 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     if (out_depth && (out_aux || out_count || (opts->flags & MGS_FLAG_SORTED)))
         return fail(MGS_ERR_INVALID_ARG, "the depth image is rendered without aux, counts or sorting");
 
-    std::array<cudaEvent_t, 4> ev{};
+    std::array<cudaEvent_t, kStageEvents> ev{};
     cudaError_t e = cudaSuccess;
     if (w->timing) {
         for (auto &x : ev) {
@@ -287,9 +291,10 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     if (s->n > 0 && (e = launch_preprocess(a, w->ctx->sm_count, stream)) != cudaSuccess)
         return cuda_fail(e, "preprocess launch");
     if (w->timing) cudaEventRecord(ev[1], stream);
-    if ((e = launch_binning(a, w->ctx->sm_count, w->bases, stream)) != cudaSuccess)
+    if ((e = launch_binning(a, w->ctx->sm_count, w->bases, stream,
+                            w->timing ? &ev[2] : nullptr)) != cudaSuccess)
         return cuda_fail(e, "binning launch");
-    if (w->timing) cudaEventRecord(ev[2], stream);
+    if (w->timing) cudaEventRecord(ev[5], stream);
     if (opts->flags & MGS_FLAG_SORTED) {
         if (out_aux) return fail(MGS_ERR_INVALID_ARG, "the sorted comparator has no aux output");
         const int64_t nc = s->n > 0 ? s->n : 1;
@@ -316,7 +321,7 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
         }
         if ((e = launch_sorted(a, w->ss, stream)) != cudaSuccess) return cuda_fail(e, "sorted launch");
         if (w->timing) {
-            cudaEventRecord(ev[3], stream);
+            cudaEventRecord(ev[6], stream);
             w->pending.push_back(ev);
         }
         w->last_tiles = T;
@@ -356,7 +361,7 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
         return cuda_fail(e, "raster launch");
     }
     if (w->timing) {
-        cudaEventRecord(ev[3], stream);
+        cudaEventRecord(ev[6], stream);
         w->pending.push_back(ev);
     }
     w->last_tiles = T;
@@ -662,17 +667,17 @@ mgs_status mgs_workspace_set_timing(mgs_workspace w, int32_t enable) {
     return MGS_OK;
 }
 
-mgs_status mgs_workspace_stage_times(mgs_workspace w, mgs_stream stream_, double ms[3],
+mgs_status mgs_workspace_stage_times(mgs_workspace w, mgs_stream stream_, double ms[6],
                                      int64_t *frames) {
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     if (!w || !ms || !frames) return fail(MGS_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard g(w->ctx->device);
     cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
-    ms[0] = ms[1] = ms[2] = 0.0;
+    for (int k = 0; k < kStageEvents - 1; ++k) ms[k] = 0.0;
     *frames = (int64_t)w->pending.size();
     for (auto &q : w->pending) {
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < kStageEvents - 1; ++k) {
             float t = 0.f;
             if ((e = cudaEventElapsedTime(&t, q[k], q[k + 1])) != cudaSuccess)
                 return cuda_fail(e, "event elapsed time");
@@ -745,6 +750,24 @@ mgs_status mgs_render_to_host(mgs_workspace w, mgs_scene s, const mgs_camera *ca
     if (st != MGS_OK) return st;
     cudaError_t e = cudaMemcpyAsync(host_rgb, w->img, (size_t)px * 12, cudaMemcpyDeviceToHost, stream);
     if (e != cudaSuccess) return cuda_fail(e, "image copy");
+    return MGS_OK;
+}
+
+mgs_status mgs_frame_stats(mgs_workspace w, mgs_stream stream_, int64_t *visible,
+                           int64_t *pairs, int64_t *fp32_sum_tiles) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!w || !visible || !pairs || !fp32_sum_tiles) return fail(MGS_ERR_INVALID_ARG, "NULL argument");
+    *visible = *pairs = *fp32_sum_tiles = 0;
+    if (!w->status || w->last_tiles == 0) return fail(MGS_ERR_INVALID_ARG, "no render yet");
+    DeviceGuard g(w->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    DevStatus h;
+    if ((e = cudaMemcpy(&h, w->status, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    *visible = (int64_t)h.last_visible;
+    *pairs = (int64_t)h.last_pairs;
+    *fp32_sum_tiles = (int64_t)h.last_wide_tiles;
     return MGS_OK;
 }
 

@@ -365,6 +365,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_order(const uint32_t *__r
         status->wmax_frame_bits = status->wmax_bits;
         status->wmax_bits = 0u;
         status->wide_bits = 0u;
+        status->last_visible = status->visible;
+        status->visible = 0u;
+        status->last_wide_tiles = 0u;
     }
     if (tid < 33) hist[tid] = 0u;
     __syncthreads();
@@ -424,6 +427,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_order(const uint32_t *__r
     for (int t = tid; t < T; t += blockDim.x) {
         const uint32_t cw = count[t], c = cw & kTileMask;
         order[atomicAdd(&start[c ? 32 - __clz(c) : 0], 1u)] = (uint32_t)t | (cw & kTileWide);
+        if (cw & kTileWide) atomicAdd(&status->last_wide_tiles, 1u);
     }
 }
 
@@ -443,7 +447,7 @@ int64_t bin_scratch_words(int64_t n, int64_t T, int sm_count) {
 }
 
 cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, const cudaEvent_t *marks) {
     const int T = a.cam.tiles_x * a.cam.tiles_y;
     const int C = bin_ctas(a.n, sm_count);
     const int64_t groups = (a.n + 31) / 32;
@@ -471,14 +475,21 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch,
             return e;
         k_bin_plan<<<1, kScanThreads, plan_smem, stream>>>(grp, groups, excl);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (marks && (e = cudaEventRecord(marks[0], stream)) != cudaSuccess) return e;
         k_bin_count<<<C, kBinThreads, smem, stream>>>(a.rect, a.rec, a.n, a.cam.tiles_x, T, excl,
                                                       groups, a.tile_count, bases, a.status,
                                                       tc_raster(a));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (marks && (e = cudaEventRecord(marks[1], stream)) != cudaSuccess) return e;
+    } else if (marks) {
+        if ((e = cudaEventRecord(marks[0], stream)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(marks[1], stream)) != cudaSuccess) return e;
     }
     k_scan_order<<<1, kScanThreads, 0, stream>>>(a.tile_count, a.tile_offsets, a.tile_order, T,
                                                  a.capacity, a.status);
-    if ((e = cudaGetLastError()) != cudaSuccess || a.n == 0) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (marks && (e = cudaEventRecord(marks[2], stream)) != cudaSuccess) return e;
+    if (a.n == 0) return e;
     k_bin_scatter<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, excl, groups,
                                                     a.tile_offsets, bases, a.gids, a.capacity,
                                                     a.status, a.rec, tc_raster(a) ? a.wt16 : nullptr);

@@ -96,6 +96,12 @@ struct DevStatus {
     // k_scan_order, which runs between the two.
     unsigned int wmax_bits;
     unsigned int wmax_frame_bits;
+    // Visible Gaussians (accumulated by preprocessing) and tiles marked
+    // kTileWide; k_scan_order hands both to last_* and resets the first.
+    unsigned int visible;
+    unsigned int last_visible;
+    unsigned int last_wide_tiles;
+    unsigned int pad;
 };
 
 // Weight range of the tensor-core sums.  The rasteriser of FP16 scenes sums
@@ -226,7 +232,10 @@ cudaError_t launch_preprocess(const RenderArgs &a, int sm_count, cudaStream_t st
 // Per-tile counts, scan and scatter.  `scratch` has bin_scratch_words(n, T,
 // sm_count) 32-bit words: the per-CTA tile bases, then the pair counts of the
 // 32-Gaussian groups and their exclusive scan.
-cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch, cudaStream_t stream);
+// marks (nullable): three events recorded on `stream` after the plan (count
+// reset, group pairs, plan scan), after the count and after the tile scan.
+cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch, cudaStream_t stream,
+                           const cudaEvent_t *marks = nullptr);
 int bin_ctas(int64_t n, int sm_count);
 __host__ __device__ constexpr int64_t bin_scratch_words_for(int64_t ctas, int64_t T, int64_t n) {
     return (ctas * T + 1) / 2 * 2 + 2 * ((n + 31) / 32 + 1) + (n + 31) / 32;

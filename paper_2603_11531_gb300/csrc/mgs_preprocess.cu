@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(kWide ? tcw::kThreads : (kTC ? tc::kThreads : 
     const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f;
     float wbound = 0.0f;
     bool any_wide = false;
+    unsigned nvis = 0;
 
     for (int64_t base = (int64_t)blockIdx.x * kStep; base < args.n;
          base += (int64_t)gridDim.x * kStep) {
@@ -302,6 +303,7 @@ __global__ void __launch_bounds__(kWide ? tcw::kThreads : (kTC ? tc::kThreads : 
                                       (wide ? kRectWide : 0u));
         if (wide) any_wide = true;
         else wbound = fmaxf(wbound, wm);
+        ++nvis;
     }
     // bound on the rasteriser's weights |w|, |w c| for this frame (Gaussians
     // that are not wide)
@@ -311,6 +313,8 @@ __global__ void __launch_bounds__(kWide ? tcw::kThreads : (kTC ? tc::kThreads : 
         atomicMax(&args.status->wmax_bits, __float_as_uint(wbound));
     if (__any_sync(0xffffffffu, any_wide) && (threadIdx.x & 31) == 0)
         atomicOr(&args.status->wide_bits, 1u);
+    nvis = __reduce_add_sync(0xffffffffu, nvis);
+    if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(&args.status->visible, nvis);
     if constexpr (kWide) {
         tcw::teardown(smem_raw, wl);
         if (!tc_ok && threadIdx.x == 0) atomicOr(&args.status->overflow, kStatusMmaTimeout);
