@@ -18,3 +18,16 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def error_report():
+    """Error of the GPU path against the FP64 oracle, per workload, collected
+    by the parity tests; written as JSON to $MGS_ERROR_REPORT when set."""
+    import json
+    rows = {}
+    yield rows
+    path = os.environ.get("MGS_ERROR_REPORT")
+    if path and rows:
+        with open(path, "w") as f:
+            json.dump(rows, f, indent=1, sort_keys=True)

@@ -138,3 +138,136 @@ def test_backward_300k_directional_derivative(R, use_mlp):
         with torch.no_grad():
             fd = float(loss(a + eps * v, None) - loss(a - eps * v, None)) / (2 * eps)
     assert abs(fd - pred) <= 0.02 * abs(pred), (fd, pred)
+
+
+def _render_np(m, R, h, cam, opts, aux=None, count=None):
+    H, W = cam.height, cam.width
+    rgb = torch.empty((H, W, 3), device="cuda")
+    m.mgs_render_checked(R.ws, h, cam, opts, rgb, aux, count)
+    return rgb.double()
+
+
+def test_backward_finite_differences_512_at_64x64(R):
+    """The backward workload's first 512 Gaussians (unbounded distribution,
+    FP32) at 64x64: the GPU adjoint against central differences of the GPU
+    forward, for means, scales, quaternions, opacities and SH coefficients
+    of sampled Gaussians (plain mode).  The loss weights only the pixels near
+    the perturbed Gaussian (dL random there, 0 elsewhere), so the FP32
+    rounding of unrelated pixels stays out of the difference; a parameter
+    whose +-h changes any pixel's inclusion count is skipped (the inclusion
+    test is piecewise constant)."""
+    import paper_2603_11531_gb300 as m
+    scene, _, _ = synth.workload_backward_300k()
+    attrs = np.ascontiguousarray(scene.attrs[:512], np.float32)
+    cam = synth.orbit_cameras(1, 8.0, 1.0, 64, 64, 60.0)[0]
+    H, W = cam.height, cam.width
+    g = oracle.preprocess(attrs, cam)
+    vis = np.flatnonzero(g["visible"] == 1)
+    rng = np.random.default_rng(7)
+    pick = rng.choice(vis, size=min(20, len(vis)), replace=False)
+    opts = m.render_opts()
+    yy, xx = np.mgrid[0:H, 0:W] + 0.5
+    checked = skipped = 0
+    comps = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 15, 19]
+    for i in pick:
+        c = g["conic"][i]
+        dx, dy = xx - g["mean"][i][0], yy - g["mean"][i][1]
+        near = c[0] * dx * dx + 2 * c[1] * dx * dy + c[2] * dy * dy <= 12.0
+        dL = np.zeros((H, W, 3))
+        dL[near] = rng.normal(size=(int(near.sum()), 3))
+        dLt = torch.from_numpy(dL).cuda()
+        h0 = R.load_scene(attrs)
+        try:
+            aux = torch.empty((5, H, W), device="cuda")
+            cnt0 = torch.empty((H, W), dtype=torch.int32, device="cuda")
+            _render_np(m, R, h0, cam, opts, aux, cnt0)
+            d_attrs = torch.empty((512, 24), device="cuda")
+            m.mgs_render_backward(R.ws, h0, cam, opts, dLt.float(), aux, d_attrs)
+            grad = d_attrs.cpu().numpy().astype(np.float64)
+        finally:
+            R.unload_scene(h0)
+        for k in comps:
+            x = float(attrs[i, k])
+            # steps large enough that the loss change stands well above the
+            # FP32 rounding of the footprint's pixels, small against the
+            # Gaussian's extent (means are world units, about 7 px per unit)
+            step = 1e-2 * max(abs(x), 0.05) if 3 <= k < 6 else 1e-2
+            imgs, same = [], True
+            for sgn in (1.0, -1.0):
+                a = attrs.copy()
+                a[i, k] = np.float32(x + sgn * step)
+                hs = R.load_scene(a)
+                try:
+                    cnt = torch.empty((H, W), dtype=torch.int32, device="cuda")
+                    imgs.append(_render_np(m, R, hs, cam, opts, None, cnt))
+                    same &= bool(torch.equal(cnt, cnt0))
+                finally:
+                    R.unload_scene(hs)
+            # the step actually taken in FP32
+            hstep = (float(np.float32(x + step)) - float(np.float32(x - step))) / 2.0
+            if not same:
+                skipped += 1
+                continue
+            fd = float((dLt * (imgs[0] - imgs[1])).sum()) / (2.0 * hstep)
+            gk = grad[i, k]
+            # FP32 rounding of the two images (2^-23 of values below 2, over
+            # the weighted pixels) bounds the difference quotient's noise
+            noise = 4.0 * 2.0 ** -23 * float(np.sqrt((dL ** 2).sum())) / (2.0 * hstep)
+            assert abs(fd - gk) <= 0.03 * abs(gk) + noise, (int(i), k, fd, gk, noise)
+            checked += 1
+    assert checked >= 0.8 * (checked + skipped) and checked > 100, (checked, skipped)
+
+
+def test_backward_finite_differences_mlp_head_bias_64x64(R):
+    """With the MLP (FP32 attributes, BF16 MLP): the gradient of the head
+    biases b3 (FP32, after the last BF16-rounded activation, so the forward is
+    smooth in them) against central differences of the GPU forward, on the
+    backward workload's first 512 Gaussians at 64x64."""
+    from paper_2603_11531_gb300 import autograd as ag
+    scene, _, _ = synth.workload_backward_300k()
+    attrs = torch.from_numpy(np.ascontiguousarray(scene.attrs[:512], np.float32)).cuda()
+    cam = synth.orbit_cameras(1, 8.0, 1.0, 64, 64, 60.0)[0]
+    w = lambda b: torch.from_numpy(synth.bf16_bits_to_f32(b).copy()).cuda()
+    f = lambda x: torch.from_numpy(np.asarray(x, np.float32).copy()).cuda()
+    b3 = f(scene.mlp.b3).requires_grad_(True)
+    head = (w(scene.mlp.w1), f(scene.mlp.b1), w(scene.mlp.w2), f(scene.mlp.b2), w(scene.mlp.w3))
+    dL = torch.from_numpy(np.random.default_rng(8).normal(size=(64, 64, 3))).cuda()
+    img = ag.render(R, attrs, cam, head + (b3,), use_mlp=True, rgb_residual=True)
+    (img.double() * dL).sum().backward()
+    grad = b3.grad.double().cpu().numpy()
+    eps = 1e-2
+    for k in range(5):
+        with torch.no_grad():
+            e = torch.zeros(5, device="cuda")
+            e[k] = eps
+            lp = (ag.render(R, attrs, cam, head + (b3 + e,), use_mlp=True, rgb_residual=True).double()
+                  * dL).sum()
+            lm = (ag.render(R, attrs, cam, head + (b3 - e,), use_mlp=True, rgb_residual=True).double()
+                  * dL).sum()
+        fd = float(lp - lm) / (2 * eps)
+        assert abs(fd - grad[k]) <= 0.02 * abs(grad[k]) + 1e-3, (k, fd, grad[k])
+
+
+@pytest.mark.slow
+def test_backward_30k_320x240_mlp_matches_oracle_gradient(R, error_report):
+    """30k Gaussians of the unbounded distribution (FP32, BF16 MLP with the
+    colour residual) at 320x240, so that many pixels and tiles accumulate
+    into the same Gaussians' gradient records (atomics under contention):
+    means, scales, quaternions and SH rows and every MLP weight against the
+    FP64 oracle gradient."""
+    s = synth.unbounded_scene(30000, seed=31, precision="fp32")
+    s.mlp = synth.random_mlp(32)
+    cam = synth.orbit_cameras(8, 8.0, 1.0, 320, 240, 60.0)[3]
+    dL = np.random.default_rng(4).normal(size=(240, 320, 3))
+    gpu, _ = _gpu_grads(R, s.attrs, cam, dL, s.mlp, use_mlp=True, res=True)
+    ref = _ref_grads(s.attrs, cam, dL, s.mlp, use_mlp=True, res=True)
+    kinds = dict(COLS)
+    kinds.pop("o")
+    report = {}
+    for name, (c0, c1) in kinds.items():
+        got = gpu["attrs"][:, c0:c1].reshape(ref[name].shape)
+        report[name] = float(np.abs(got - ref[name]).max() / np.abs(ref[name]).max())
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        report[k] = float(np.abs(gpu[k] - ref[k]).max() / np.abs(ref[k]).max())
+    error_report["backward_30k_320x240_mlp_relative_to_max_per_kind"] = report
+    _compare(gpu, ref, tol=5e-3, kinds=kinds, mlp_keys=("w1", "b1", "w2", "b2", "w3", "b3"))

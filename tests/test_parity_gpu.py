@@ -207,10 +207,11 @@ def test_render_to_host_matches_device(R, torch_cuda):
 
 
 @pytest.mark.slow
-def test_unbounded_600k_full_size_sampled(R):
+def test_unbounded_600k_full_size_sampled(R, error_report):
     """The benchmark workload (600k FP16 Gaussians, BF16 MLP, 1600x1063):
     all tile lists exact; counts and pixels on a sample of tiles."""
     scene, cams = synth.workload_unbounded_600k(n_poses=64)
+    errs = []
     for pose in (0, 21):
         cam = cams[pose]
         h = R.load_scene(scene)
@@ -234,10 +235,15 @@ def test_unbounded_600k_full_size_sampled(R):
                 x0, y0 = (t % tx) * 16, (t // tx) * 16
                 sl = (slice(y0, min(y0 + 16, cam.height)), slice(x0, min(x0 + 16, cam.width)))
                 np.testing.assert_array_equal(cnt[sl], ref_cnt[sl])
-                err = np.abs(rgb[sl] - ref_rgb[sl]).max()
-                assert err <= TOL_FP16_MLP, (t, err)
+                e = np.abs(rgb[sl] - ref_rgb[sl])
+                assert e.max() <= TOL_FP16_MLP, (t, e.max())
+                errs.append(e.ravel())
         finally:
             R.unload_scene(h)
+    flat = np.concatenate(errs)
+    error_report["unbounded_600k_1600x1063_fp16_mlp"] = {
+        "poses": [0, 21], "tiles_per_pose": "heaviest 6 + 24 random + 4 of the ragged last row",
+        "max_abs": float(flat.max()), "mean_abs": float(flat.mean())}
 
 
 def test_repeat_renders_agree(R, torch_cuda):
