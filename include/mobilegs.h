@@ -312,10 +312,16 @@ typedef struct {
 
 /* Start a server on the context's device.  A worker thread owned by the
  * server admits queued requests, in arrival order, into free slots while their
- * estimated scratch fits the budget, runs their preprocessing and binning as
- * CUDA graphs, rasterises each group admitted together in one persistent
- * batched launch, and records completion.  Not in the paper: the serving
- * pattern of the workload. */
+ * estimated scratch fits the budget.  Every slot works on its own stream, so
+ * the requests in flight overlap on the device.  A view of more than 2,048
+ * tiles runs alone: preprocessing, MLP, binning and rasterisation as one CUDA
+ * graph.  Consecutive smaller views (up to max_batch) form a group: their
+ * preprocessing and binning run as graphs on their slots' streams, and one
+ * launch of the persistent batched rasteriser draws all their tiles.  Graphs
+ * are instantiated once per (slot, scene, resolution, options) and relaunched
+ * with the new camera and output set in the kernel nodes that read them.
+ * Completion is recorded per group.  Not in the paper: the serving pattern of
+ * the workload. */
 mgs_status mgs_server_create(mgs_ctx ctx, const mgs_server_config *cfg, mgs_server *out);
 /* Finish every queued and running request, then release the server. */
 mgs_status mgs_server_destroy(mgs_server srv);

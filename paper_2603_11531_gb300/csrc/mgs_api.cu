@@ -112,6 +112,7 @@ struct mgs_workspace_s {
     int64_t last_tiles = 0;
     const uint32_t *last_perm = nullptr;   // storage -> caller order of the last scene
     uint64_t grow_hint = 0;  // pairs needed by an overflowed render
+    uint64_t generation = 0; // bumped whenever a scratch buffer is reallocated
     bool timing = false;
     std::vector<cudaEvent_t> event_pool;
     std::vector<std::array<cudaEvent_t, kStageEvents>> pending;  // per timed render
@@ -127,6 +128,22 @@ int64_t ws_bytes(const mgs_workspace_s *w) {
 
 mgs_status ws_ensure(mgs_workspace_s *w, int64_t n, int64_t tiles, uint64_t pairs) {
     cudaError_t e;
+    const uint64_t gen0 = w->generation;
+    struct Bump {   // any reallocation below invalidates captured launches
+        mgs_workspace_s *w;
+        uint64_t gen0;
+        const void *p[7];
+        int64_t c[4];
+        ~Bump() {
+            const void *q[7] = {w->rec, w->rect, w->wt16, w->tile_count, w->gids, w->bases, w->status};
+            const int64_t d[4] = {w->n_cap, w->tiles_cap, (int64_t)w->pair_cap, w->bases_cap};
+            bool changed = false;
+            for (int k = 0; k < 7; ++k) changed |= q[k] != p[k];
+            for (int k = 0; k < 4; ++k) changed |= d[k] != c[k];
+            if (changed) w->generation = gen0 + 1;
+        }
+    } bump{w, gen0, {w->rec, w->rect, w->wt16, w->tile_count, w->gids, w->bases, w->status},
+           {w->n_cap, w->tiles_cap, (int64_t)w->pair_cap, w->bases_cap}};
     if (n > w->n_cap) {
         dev_free(w->rec);
         dev_free(w->rect);
@@ -219,7 +236,7 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
                        const mgs_render_opts *opts, float *out_rgb, float *out_aux,
                        int32_t *out_count, cudaStream_t stream,
                        const BackwardIO *bwd = nullptr, RenderArgs *prep = nullptr,
-                       float *out_depth = nullptr) {
+                       float *out_depth = nullptr, bool args_only = false) {
     if (!w || !s) return fail(MGS_ERR_INVALID_ARG, "workspace or scene is NULL");
     if (w->ctx != s->ctx) return fail(MGS_ERR_INVALID_ARG, "scene and workspace belong to different contexts");
     mgs_status st = check_camera(cam);
@@ -274,6 +291,10 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
     a.out_depth = out_depth;
     if (out_depth && (out_aux || out_count || (opts->flags & MGS_FLAG_SORTED)))
         return fail(MGS_ERR_INVALID_ARG, "the depth image is rendered without aux, counts or sorting");
+    if (prep && args_only) {   // arguments of this view; nothing is launched
+        *prep = a;
+        return MGS_OK;
+    }
 
     std::array<cudaEvent_t, kStageEvents> ev{};
     cudaError_t e = cudaSuccess;
@@ -375,12 +396,14 @@ void mgs::set_last_error(const char *msg) { g_err = msg; }
 
 mgs_status mgs::prepare_view(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
                              const mgs_render_opts *opts, float *out_rgb, cudaStream_t stream,
-                             RenderArgs *args_out) {
+                             RenderArgs *args_out, bool args_only) {
     mgs_status st = render_impl(w, s, cam, opts, out_rgb, nullptr, nullptr, stream, nullptr,
-                                args_out);
+                                args_out, nullptr, args_only);
     if (st == MGS_OK) args_out->out_rgb = out_rgb;
     return st;
 }
+
+uint64_t mgs::workspace_generation(mgs_workspace w) { return w->generation; }
 
 int mgs::ctx_device(mgs_ctx c) { return c->device; }
 int mgs::ctx_sm_count(mgs_ctx c) { return c->sm_count; }

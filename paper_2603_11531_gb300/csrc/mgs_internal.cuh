@@ -254,10 +254,14 @@ int pre_bwd_blocks(int64_t n, int sm_count);
 void set_last_error(const char *msg);
 // Preprocessing and binning of one view into workspace w (no rasterisation,
 // no allocation if the workspace is large enough); *args_out receives the
-// arguments the rasteriser needs.  Stream-ordered, capturable.
+// arguments the rasteriser needs.  Stream-ordered, capturable.  args_only:
+// check the arguments, size the workspace and fill *args_out, launch nothing.
 mgs_status prepare_view(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
                         const mgs_render_opts *opts, float *out_rgb, cudaStream_t stream,
-                        RenderArgs *args_out);
+                        RenderArgs *args_out, bool args_only = false);
+// Changes whenever one of the workspace's scratch buffers is reallocated
+// (launches captured before then address freed memory).
+uint64_t workspace_generation(mgs_workspace w);
 int ctx_device(mgs_ctx c);
 int ctx_sm_count(mgs_ctx c);
 int64_t scene_size(mgs_scene s);

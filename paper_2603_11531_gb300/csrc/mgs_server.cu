@@ -5,20 +5,25 @@
 //   1. admits queued requests in arrival order into free slots, as long as the
 //      slots' workspaces fit the server's device-memory budget (a request that
 //      cannot fit even alone is refused with MGS_ERR_OOM);
-//   2. runs each admitted request's preprocessing, MLP and tile binning as a
-//      CUDA graph on its slot's stream (captured per request and applied to
-//      the slot's executable graph with cudaGraphExecUpdate);
-//   3. rasterises every group admitted together with one launch of the
-//      persistent batched rasteriser, whose CTAs pull (view, tile) items from
-//      a shared counter, so views of different scenes and resolutions share
-//      the GPU;
+//   2. forms a group from the admitted requests: a view of more than
+//      kSmallTiles tiles goes alone; consecutive small views (up to max_batch)
+//      go together;
+//   3. runs every slot's work on the slot's own stream, so the requests in
+//      flight overlap on the device: a lone view runs preprocessing, the MLP,
+//      binning and its rasteriser as one CUDA graph; the views of a group run
+//      preprocessing and binning as graphs on their streams, and the group
+//      is rasterised by one launch of the persistent batched rasteriser,
+//      whose CTAs pull (view, tile) items from a shared counter (the small
+//      views' tiles fill each other's tails);
 //   4. polls completion events, stamps completion times, re-queues a request
 //      whose tile lists overflowed its workspace (with a larger capacity),
 //      and frees the slots.
-// Groups admitted at different times run concurrently on their own streams,
-// so new requests start while earlier ones are still on the GPU.  Each view's
-// image depends only on its own tile lists: alone or in a mix it is the same
-// up to FP32 rounding of the accumulation order.
+// Graphs are instantiated once per (slot, scene, resolution, options) and
+// relaunched with the new camera and output written into the kernel nodes
+// that read them (preprocessing and rasterisation); binning reads only the
+// workspace, which the key pins.  Each view's image depends only on its own
+// tile lists: alone or in a mix it is the same up to FP32 rounding of the
+// accumulation order.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -42,6 +47,11 @@ double now_s() {
 
 enum { kQueued = 0, kRunning = 1, kDone = 2 };
 
+// Views up to this many tiles (e.g. 640x480: 1,200) are rasterised together
+// when several are admitted at once; larger views fill the GPU alone.
+constexpr int kSmallTiles = 2048;
+constexpr int kGraphsPerSlot = 16;
+
 struct Request {
     int64_t ticket = 0;
     mgs_scene scene = nullptr;
@@ -55,21 +65,32 @@ struct Request {
     int attempts = 0;
 };
 
+// A cached executable graph of one slot: preprocessing + binning (+ the
+// single-view rasteriser when `raster`), with the nodes whose arguments
+// depend on the camera and the output.
+struct SlotGraph {
+    uint64_t key = 0;
+    uint64_t gen = 0;           // workspace buffer generation it was captured with
+    uint64_t last_use = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> arg_nodes;   // kernel nodes taking RenderArgs
+};
+
 struct Slot {
     mgs_workspace ws = nullptr;
     cudaStream_t stream = nullptr;
-    cudaGraphExec_t exec = nullptr;
     cudaEvent_t prepared = nullptr;
     DevStatus *status_host = nullptr;  // pinned
     bool busy = false;
     int64_t ticket = 0;
     RenderArgs args{};
+    std::vector<SlotGraph> graphs;
 };
 
-struct Batch {
+struct Group {
     bool active = false;
     std::vector<int> slots;
-    cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     RenderArgs *args_host = nullptr;  // pinned
     int *prefix_host = nullptr;       // pinned
@@ -87,13 +108,14 @@ struct mgs_server_s {
     int64_t budget = 0;
     int max_batch = 8;
     std::vector<Slot> slots;
-    std::vector<Batch> batches;
+    std::vector<Group> groups;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<int64_t> queue;
     std::unordered_map<int64_t, Request> reqs;
     int64_t next_ticket = 1;
     int64_t completed = 0;
+    uint64_t clock = 0;
     bool stop = false;
     bool graphs = true;
     std::unordered_map<uint64_t, uint64_t> pairs_cache;  // (scene, size) -> pairs
@@ -113,53 +135,142 @@ uint64_t cache_key(mgs_scene s, int w, int h) {
     return (reinterpret_cast<uint64_t>(s) * 1000003ull) ^ ((uint64_t)w << 32) ^ (uint64_t)h;
 }
 
+uint64_t graph_key(const Request &rq, bool raster) {
+    uint64_t k = cache_key(rq.scene, rq.cam.width, rq.cam.height);
+    k = k * 31ull + (uint64_t)rq.opts.use_mlp;
+    k = k * 31ull + (uint64_t)rq.opts.mlp_rgb_residual;
+    k = k * 131ull + (uint64_t)rq.opts.flags;
+    return k * 2ull + (raster ? 1ull : 0ull);
+}
+
 int64_t estimate_bytes(int64_t n, int w, int h, uint64_t pairs, int sm_count) {
     const int64_t T = (int64_t)((w + kTile - 1) / kTile) * ((h + kTile - 1) / kTile);
-    return n * (int64_t)(sizeof(ProjRec) + sizeof(uint2)) + (T + 1) * 12 +
+    return n * (int64_t)(sizeof(ProjRec) + sizeof(uint2) + sizeof(uint4)) + (T + 1) * 12 +
            bin_scratch_words(n, T, sm_count) * 4 + (int64_t)pairs * 4 + 4096;
 }
 
-// Runs the request's preprocessing and binning on the slot's stream, as a
-// captured graph when possible.
-mgs_status launch_prepare(mgs_server_s *S, Slot &slot, Request &rq) {
-    if (S->graphs) {
-        cudaGraph_t g = nullptr;
-        RenderArgs a{};
-        cudaError_t e = cudaStreamBeginCapture(slot.stream, cudaStreamCaptureModeThreadLocal);
-        mgs_status st = MGS_ERR_CUDA;
-        if (e == cudaSuccess) {
-            st = prepare_view(slot.ws, rq.scene, &rq.cam, &rq.opts, rq.out, slot.stream, &a);
-            e = cudaStreamEndCapture(slot.stream, &g);
-        }
-        if (e == cudaSuccess && st != MGS_OK) {      // argument error, not a capture problem
-            if (g) cudaGraphDestroy(g);
-            return st;
-        }
-        if (e == cudaSuccess && st == MGS_OK && g) {
-            bool ok = false;
-            if (slot.exec) {
-                cudaGraphExecUpdateResultInfo info;
-                ok = cudaGraphExecUpdate(slot.exec, g, &info) == cudaSuccess;
-                if (!ok) {
-                    cudaGetLastError();
-                    cudaGraphExecDestroy(slot.exec);
-                    slot.exec = nullptr;
-                }
-            }
-            if (!ok) ok = cudaGraphInstantiate(&slot.exec, g, 0) == cudaSuccess;
-            cudaGraphDestroy(g);
-            if (ok && cudaGraphLaunch(slot.exec, slot.stream) == cudaSuccess) {
-                slot.args = a;
-                return MGS_OK;
-            }
-        } else if (g) {
-            cudaGraphDestroy(g);
-        }
-        // capture unavailable here: fall back to direct launches from now on
-        cudaGetLastError();
-        S->graphs = false;
+void drop_graphs(Slot &sl) {
+    for (SlotGraph &g : sl.graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
     }
-    return prepare_view(slot.ws, rq.scene, &rq.cam, &rq.opts, rq.out, slot.stream, &slot.args);
+    sl.graphs.clear();
+}
+
+// Kernel nodes of a captured graph whose only argument is a RenderArgs (the
+// preprocessing and rasterisation kernels), found by their parameter size.
+std::vector<cudaGraphNode_t> render_arg_nodes(cudaGraph_t g) {
+    std::vector<cudaGraphNode_t> out;
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return out;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return out;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams p{};
+        if (cudaGraphKernelNodeGetParams(nd, &p) != cudaSuccess) continue;
+        size_t off = 0, sz = 0;
+        // exactly one parameter of sizeof(RenderArgs)
+        if (cudaFuncGetParamInfo(p.func, 0, &off, &sz) == cudaSuccess && sz == sizeof(RenderArgs) &&
+            cudaFuncGetParamInfo(p.func, 1, &off, &sz) != cudaSuccess)
+            out.push_back(nd);
+        cudaGetLastError();
+    }
+    return out;
+}
+
+// The request's work on the slot's stream: preprocessing and binning, and the
+// single-view rasteriser when `raster`.  Through the slot's cached graph for
+// this key when graphs are usable, else by direct launches.
+mgs_status launch_view(mgs_server_s *S, Slot &sl, Request &rq, bool raster) {
+    // Stream-ordered preparation; sets sl.args (needed for the batched raster
+    // and the status read-back) and grows the workspace if it must.
+    auto direct = [&]() -> mgs_status {
+        mgs_status st = prepare_view(sl.ws, rq.scene, &rq.cam, &rq.opts, rq.out, sl.stream, &sl.args);
+        if (st == MGS_OK && raster && launch_raster(sl.args, sl.stream) != cudaSuccess)
+            st = MGS_ERR_CUDA;
+        return st;
+    };
+    if (!S->graphs) return direct();
+    const uint64_t key = graph_key(rq, raster);
+    const uint64_t gen = workspace_generation(sl.ws);
+    SlotGraph *hit = nullptr;
+    for (SlotGraph &g : sl.graphs)
+        if (g.key == key && g.gen == gen) hit = &g;
+    if (hit) {
+        // same scene, size, options and workspace buffers: new camera / output
+        RenderArgs a{};
+        mgs_status st = prepare_view(sl.ws, rq.scene, &rq.cam, &rq.opts, rq.out, nullptr, &a, true);
+        if (st != MGS_OK) return st;
+        bool ok = workspace_generation(sl.ws) == gen;
+        void *params[1] = {&a};
+        for (cudaGraphNode_t nd : hit->arg_nodes) {
+            if (!ok) break;
+            cudaKernelNodeParams p{};
+            ok = cudaGraphKernelNodeGetParams(nd, &p) == cudaSuccess;
+            p.kernelParams = params;
+            p.extra = nullptr;
+            ok = ok && cudaGraphExecKernelNodeSetParams(hit->exec, nd, &p) == cudaSuccess;
+        }
+        if (ok && cudaGraphLaunch(hit->exec, sl.stream) == cudaSuccess) {
+            sl.args = a;
+            hit->last_use = ++S->clock;
+            return MGS_OK;
+        }
+        cudaGetLastError();
+        hit->key = 0;   // unusable: recapture below
+    }
+    // capture this key's graph (the workspace is sized first, outside capture)
+    {
+        RenderArgs a{};
+        mgs_status st = prepare_view(sl.ws, rq.scene, &rq.cam, &rq.opts, rq.out, nullptr, &a, true);
+        if (st != MGS_OK) return st;
+    }
+    cudaGraph_t g = nullptr;
+    RenderArgs a{};
+    mgs_status st = MGS_ERR_CUDA;
+    cudaError_t e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = prepare_view(sl.ws, rq.scene, &rq.cam, &rq.opts, rq.out, sl.stream, &a);
+        if (st == MGS_OK && raster && launch_raster(a, sl.stream) != cudaSuccess) st = MGS_ERR_CUDA;
+        e = cudaStreamEndCapture(sl.stream, &g);
+    }
+    if (e == cudaSuccess && st != MGS_OK) {   // argument error, not a capture problem
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess &&
+        cudaGraphLaunch(exec, sl.stream) == cudaSuccess) {
+        SlotGraph sg;
+        sg.key = key;
+        sg.gen = workspace_generation(sl.ws);
+        sg.graph = g;
+        sg.exec = exec;
+        sg.arg_nodes = render_arg_nodes(g);
+        sg.last_use = ++S->clock;
+        if ((int)sl.graphs.size() >= kGraphsPerSlot) {   // evict the least recently used
+            auto lru = std::min_element(sl.graphs.begin(), sl.graphs.end(),
+                                        [](const SlotGraph &x, const SlotGraph &y) {
+                                            return x.last_use < y.last_use;
+                                        });
+            if (lru->exec) cudaGraphExecDestroy(lru->exec);
+            if (lru->graph) cudaGraphDestroy(lru->graph);
+            *lru = sg;
+        } else {
+            sl.graphs.push_back(sg);
+        }
+        sl.args = a;
+        return MGS_OK;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+    // capture unavailable here: direct launches from now on
+    cudaGetLastError();
+    S->graphs = false;
+    for (Slot &x : S->slots) drop_graphs(x);
+    return direct();
 }
 
 }  // namespace
@@ -170,7 +281,7 @@ void mgs_server_s::run() {
     for (;;) {
         bool progress = false;
         // 1. retire finished groups
-        for (Batch &b : batches) {
+        for (Group &b : groups) {
             if (!b.active) continue;
             cudaError_t q = cudaEventQuery(b.done);
             if (q == cudaErrorNotReady) continue;
@@ -206,23 +317,29 @@ void mgs_server_s::run() {
             progress = true;
             cv_done.notify_all();
         }
-        // 2. admit
+        // 2. admit one group: the queue's head, and after a small view the
+        //    following small views, up to max_batch
         admitted.clear();
         int bi = -1;
         {
             std::unique_lock<std::mutex> lk(mu);
             if (stop && queue.empty()) {
                 bool any = false;
-                for (const Batch &b : batches) any |= b.active;
+                for (const Group &b : groups) any |= b.active;
                 if (!any) return;
             }
-            for (int k = 0; k < (int)batches.size(); ++k)
-                if (!batches[k].active) {
+            for (int k = 0; k < (int)groups.size(); ++k)
+                if (!groups[k].active) {
                     bi = k;
                     break;
                 }
             bool released = false;
+            bool small_group = false;
             while (bi >= 0 && !queue.empty() && (int)admitted.size() < max_batch) {
+                Request &rq = reqs[queue.front()];
+                const int tiles = ((rq.cam.width + kTile - 1) / kTile) * ((rq.cam.height + kTile - 1) / kTile);
+                const bool small = tiles <= kSmallTiles && (rq.opts.flags & MGS_FLAG_SORTED) == 0;
+                if (!admitted.empty() && (!small_group || !small)) break;
                 int free_slot = -1;
                 for (int k = 0; k < (int)slots.size(); ++k)
                     if (!slots[k].busy &&
@@ -231,7 +348,6 @@ void mgs_server_s::run() {
                          mgs_workspace_bytes(slots[k].ws) > mgs_workspace_bytes(slots[free_slot].ws)))
                         free_slot = k;
                 if (free_slot < 0) break;
-                Request &rq = reqs[queue.front()];
                 const int64_t n = scene_size(rq.scene);
                 auto it = pairs_cache.find(cache_key(rq.scene, rq.cam.width, rq.cam.height));
                 uint64_t pairs = it != pairs_cache.end() ? it->second + it->second / 8 + 1024
@@ -255,12 +371,9 @@ void mgs_server_s::run() {
                     if (any_busy || !admitted.empty() || released) break;
                     released = true;
                     for (Slot &s : slots) {
+                        drop_graphs(s);
                         mgs_workspace_destroy(s.ws);
                         mgs_workspace_create(ctx, &s.ws);
-                        if (s.exec) {
-                            cudaGraphExecDestroy(s.exec);
-                            s.exec = nullptr;
-                        }
                     }
                     continue;
                 }
@@ -270,12 +383,9 @@ void mgs_server_s::run() {
                 if (rs == MGS_OK && reserved_bytes() > budget) {
                     // capacities only grow: rebuild this slot's scratch at exactly
                     // this request's size so the total stays within the budget
+                    drop_graphs(sl);
                     mgs_workspace_destroy(sl.ws);
                     mgs_workspace_create(ctx, &sl.ws);
-                    if (sl.exec) {
-                        cudaGraphExecDestroy(sl.exec);
-                        sl.exec = nullptr;
-                    }
                     rs = mgs_workspace_reserve(sl.ws, n, rq.cam.width, rq.cam.height, (int64_t)pairs);
                 }
                 if (rs != MGS_OK) {
@@ -294,11 +404,13 @@ void mgs_server_s::run() {
                 sl.busy = true;
                 sl.ticket = rq.ticket;
                 admitted.push_back(free_slot);
+                if (admitted.size() == 1) small_group = small;
             }
         }
         // 3. launch the admitted group
         if (!admitted.empty()) {
-            Batch &b = batches[bi];
+            Group &b = groups[bi];
+            const bool alone = admitted.size() == 1;
             std::vector<int> ok;
             for (int si : admitted) {
                 Slot &sl = slots[si];
@@ -307,9 +419,9 @@ void mgs_server_s::run() {
                     std::lock_guard<std::mutex> lk(mu);
                     rq = &reqs[sl.ticket];
                 }
-                mgs_status st = launch_prepare(this, sl, *rq);
-                if (st == MGS_OK) st = cudaEventRecord(sl.prepared, sl.stream) == cudaSuccess ? MGS_OK : MGS_ERR_CUDA;
-                if (st == MGS_OK && cudaStreamWaitEvent(b.stream, sl.prepared, 0) != cudaSuccess)
+                mgs_status st = launch_view(this, sl, *rq, alone);
+                if (st == MGS_OK && !alone &&
+                    cudaEventRecord(sl.prepared, sl.stream) != cudaSuccess)
                     st = MGS_ERR_CUDA;
                 if (st != MGS_OK) {
                     std::lock_guard<std::mutex> lk(mu);
@@ -324,22 +436,29 @@ void mgs_server_s::run() {
                 ok.push_back(si);
             }
             if (!ok.empty()) {
-                b.prefix_host[0] = 0;
-                for (size_t v = 0; v < ok.size(); ++v) {
-                    const RenderArgs &a = slots[ok[v]].args;
-                    b.args_host[v] = a;
-                    b.prefix_host[v + 1] = b.prefix_host[v] + a.cam.tiles_x * a.cam.tiles_y;
+                Slot &lead = slots[ok[0]];
+                if (!alone) {
+                    // the group's views rasterised together on the first view's stream
+                    for (size_t v = 1; v < ok.size(); ++v)
+                        cudaStreamWaitEvent(lead.stream, slots[ok[v]].prepared, 0);
+                    b.prefix_host[0] = 0;
+                    for (size_t v = 0; v < ok.size(); ++v) {
+                        const RenderArgs &a = slots[ok[v]].args;
+                        b.args_host[v] = a;
+                        b.prefix_host[v + 1] = b.prefix_host[v] + a.cam.tiles_x * a.cam.tiles_y;
+                    }
+                    const int nv = (int)ok.size();
+                    cudaMemcpyAsync(b.args_dev, b.args_host, sizeof(RenderArgs) * nv,
+                                    cudaMemcpyHostToDevice, lead.stream);
+                    cudaMemcpyAsync(b.prefix_dev, b.prefix_host, sizeof(int) * (nv + 1),
+                                    cudaMemcpyHostToDevice, lead.stream);
+                    launch_raster_batch(b.args_dev, b.prefix_dev, nv, b.counter_dev, sm_count,
+                                        lead.stream);
                 }
-                const int nv = (int)ok.size();
-                cudaMemcpyAsync(b.args_dev, b.args_host, sizeof(RenderArgs) * nv,
-                                cudaMemcpyHostToDevice, b.stream);
-                cudaMemcpyAsync(b.prefix_dev, b.prefix_host, sizeof(int) * (nv + 1),
-                                cudaMemcpyHostToDevice, b.stream);
-                launch_raster_batch(b.args_dev, b.prefix_dev, nv, b.counter_dev, sm_count, b.stream);
                 for (int si : ok)
                     cudaMemcpyAsync(slots[si].status_host, slots[si].args.status, sizeof(DevStatus),
-                                    cudaMemcpyDeviceToHost, b.stream);
-                cudaEventRecord(b.done, b.stream);
+                                    cudaMemcpyDeviceToHost, lead.stream);
+                cudaEventRecord(b.done, lead.stream);
                 b.slots = ok;
                 b.active = true;
             }
@@ -348,7 +467,7 @@ void mgs_server_s::run() {
         if (!progress) {
             std::unique_lock<std::mutex> lk(mu);
             bool inflight = false;
-            for (const Batch &b : batches) inflight |= b.active;
+            for (const Group &b : groups) inflight |= b.active;
             if (inflight)
                 cv_work.wait_for(lk, std::chrono::microseconds(20));
             else
@@ -388,9 +507,8 @@ mgs_status mgs_server_create(mgs_ctx ctx, const mgs_server_config *cfg, mgs_serv
         ok &= cudaEventCreateWithFlags(&s.prepared, cudaEventDisableTiming) == cudaSuccess;
         ok &= cudaMallocHost(&s.status_host, sizeof(DevStatus)) == cudaSuccess;
     }
-    S->batches.resize(cfg->slots);
-    for (Batch &b : S->batches) {
-        ok &= cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) == cudaSuccess;
+    S->groups.resize(cfg->slots);
+    for (Group &b : S->groups) {
         ok &= cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) == cudaSuccess;
         ok &= cudaMallocHost(&b.args_host, sizeof(RenderArgs) * cfg->max_batch) == cudaSuccess;
         ok &= cudaMallocHost(&b.prefix_host, sizeof(int) * (cfg->max_batch + 1)) == cudaSuccess;
@@ -422,17 +540,13 @@ mgs_status mgs_server_destroy(mgs_server S) {
     cudaSetDevice(S->device);
     for (Slot &s : S->slots) {
         if (s.stream) cudaStreamSynchronize(s.stream);
-        if (s.exec) cudaGraphExecDestroy(s.exec);
+        drop_graphs(s);
         if (s.ws) mgs_workspace_destroy(s.ws);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.prepared) cudaEventDestroy(s.prepared);
         if (s.status_host) cudaFreeHost(s.status_host);
     }
-    for (Batch &b : S->batches) {
-        if (b.stream) {
-            cudaStreamSynchronize(b.stream);
-            cudaStreamDestroy(b.stream);
-        }
+    for (Group &b : S->groups) {
         if (b.done) cudaEventDestroy(b.done);
         if (b.args_host) cudaFreeHost(b.args_host);
         if (b.prefix_host) cudaFreeHost(b.prefix_host);
