@@ -127,7 +127,7 @@ typedef struct {
     float t[3];
     float fx, fy, cx, cy;
     int32_t width, height;   /* 1 .. 16384 */
-    float znear;             /* Gaussians with view z <= znear are culled */
+    float znear;             /* > 0: Gaussians with view z <= znear are culled */
 } mgs_camera;
 
 typedef struct {

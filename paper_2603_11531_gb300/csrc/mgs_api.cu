@@ -193,8 +193,11 @@ mgs_status check_camera(const mgs_camera *c) {
         return fail(MGS_ERR_INVALID_ARG, "image size %dx%d outside 1..16384", c->width, c->height);
     if (!finite_pos(c->fx) || !finite_pos(c->fy))
         return fail(MGS_ERR_INVALID_ARG, "focal lengths must be finite and > 0");
-    if (!std::isfinite(c->cx) || !std::isfinite(c->cy) || !std::isfinite(c->znear))
-        return fail(MGS_ERR_INVALID_ARG, "principal point and znear must be finite");
+    if (!std::isfinite(c->cx) || !std::isfinite(c->cy))
+        return fail(MGS_ERR_INVALID_ARG, "principal point must be finite");
+    // the pinhole projection divides by the view depth: the near plane must
+    // lie in front of the camera (this also keeps Eq. 3's depth d > 0)
+    if (!finite_pos(c->znear)) return fail(MGS_ERR_INVALID_ARG, "znear must be finite and > 0");
     for (int i = 0; i < 9; ++i)
         if (!std::isfinite(c->R[i])) return fail(MGS_ERR_INVALID_ARG, "R must be finite");
     for (int i = 0; i < 3; ++i)
@@ -393,6 +396,8 @@ mgs_status render_impl(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
 }  // namespace
 
 void mgs::set_last_error(const char *msg) { g_err = msg; }
+
+mgs_status mgs::validate_camera(const mgs_camera *c) { return check_camera(c); }
 
 mgs_status mgs::prepare_view(mgs_workspace w, mgs_scene s, const mgs_camera *cam,
                              const mgs_render_opts *opts, float *out_rgb, cudaStream_t stream,

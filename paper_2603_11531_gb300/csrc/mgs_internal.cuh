@@ -252,6 +252,10 @@ int grad_record_size();
 int pre_bwd_blocks(int64_t n, int sm_count);
 // Sets the calling thread's message returned by mgs_last_error().
 void set_last_error(const char *msg);
+// Host-side camera check shared by every entry point: image size 1..16384,
+// finite pose and intrinsics, focal lengths > 0, 0 < znear (finite).  Sets the
+// error message on failure.
+mgs_status validate_camera(const mgs_camera *c);
 // Preprocessing and binning of one view into workspace w (no rasterisation,
 // no allocation if the workspace is large enough); *args_out receives the
 // arguments the rasteriser needs.  Stream-ordered, capturable.  args_only:

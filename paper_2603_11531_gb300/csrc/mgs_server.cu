@@ -569,11 +569,7 @@ mgs_status mgs_server_submit(mgs_server S, mgs_scene scene, const mgs_camera *ca
         set_last_error("scene belongs to another context");
         return MGS_ERR_INVALID_ARG;
     }
-    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384 ||
-        !(cam->fx > 0.0f) || !(cam->fy > 0.0f)) {
-        set_last_error("bad camera");
-        return MGS_ERR_INVALID_ARG;
-    }
+    if (validate_camera(cam) != MGS_OK) return MGS_ERR_INVALID_ARG;
     Request rq;
     rq.scene = scene;
     rq.cam = *cam;

@@ -92,8 +92,7 @@ extern "C" mgs_status mgs_render_static(const void *attrs, int64_t n, int32_t pr
     if (n > 0 && (!attrs || (reinterpret_cast<uintptr_t>(attrs) & 15)))
         return fail_static(MGS_ERR_INVALID_ARG, "attrs must be a 16-byte aligned device pointer");
     if (!cam || !opts || !out_rgb) return fail_static(MGS_ERR_INVALID_ARG, "NULL argument");
-    if (cam->width < 1 || cam->height < 1 || !(cam->fx > 0.0f) || !(cam->fy > 0.0f))
-        return fail_static(MGS_ERR_INVALID_ARG, "bad camera");
+    if (validate_camera(cam) != MGS_OK) return MGS_ERR_INVALID_ARG;
     const int tiles_x = (cam->width + kTile - 1) / kTile;
     const int tiles_y = (cam->height + kTile - 1) / kTile;
     if ((int64_t)tiles_x * tiles_y > kMaxTiles)

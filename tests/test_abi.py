@@ -107,3 +107,28 @@ def test_binding_rejects_bad_output_buffers_before_any_call(monkeypatch):
                               torch.empty((5, 24, 32)), torch.empty((100, 24)))
     with pytest.raises(ValueError):          # handle this module never created
         m.mgs_render(object(), sc_h, cam, opts, torch.empty((24, 32, 3)))
+
+
+def test_camera_checks_run_before_any_device_work(built):
+    """A camera with znear <= 0 (the projection divides by the view depth)
+    or a non-finite pose is refused by the host-side check that every entry
+    point shares, before any CUDA call (so it is testable without a GPU)."""
+    import ctypes
+    import math
+
+    import paper_2603_11531_gb300 as m
+    from paper_2603_11531_gb300 import synth
+    L = m.lib()
+    good = m.camera_struct(synth.look_at((0, 0, -3), (0, 0, 0), 64, 48, 60.0))
+    fake_out = ctypes.c_void_p(256)     # never dereferenced: the check fails first
+    for field, value in (("znear", 0.0), ("znear", -1.0), ("znear", math.inf), ("fx", math.nan)):
+        cam = m.mgs_camera.from_buffer_copy(good)
+        setattr(cam, field, value)
+        st = L.mgs_render_static(None, 0, m.MGS_PREC_FP32, ctypes.byref(cam),
+                                 ctypes.byref(m.render_opts()), fake_out, None)
+        assert st == m.MGS_ERR_INVALID_ARG, (field, value)
+    cam = m.mgs_camera.from_buffer_copy(good)
+    cam.t[1] = math.inf
+    st = L.mgs_render_static(None, 0, m.MGS_PREC_FP32, ctypes.byref(cam),
+                             ctypes.byref(m.render_opts()), fake_out, None)
+    assert st == m.MGS_ERR_INVALID_ARG
