@@ -241,14 +241,20 @@ mgs_status launch_view(mgs_server_s *S, Slot &sl, Request &rq, bool raster) {
         return st;
     }
     cudaGraphExec_t exec = nullptr;
-    if (e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess &&
+    // the nodes that take the camera and output must all be found, else a
+    // relaunch would draw with stale arguments: then no graphs at all
+    std::vector<cudaGraphNode_t> arg_nodes;
+    const size_t want = (scene_size(rq.scene) > 0 ? 1u : 0u) + (raster ? 1u : 0u);
+    if (e == cudaSuccess && g) arg_nodes = render_arg_nodes(g);
+    if (e == cudaSuccess && g && arg_nodes.size() == want &&
+        cudaGraphInstantiate(&exec, g, 0) == cudaSuccess &&
         cudaGraphLaunch(exec, sl.stream) == cudaSuccess) {
         SlotGraph sg;
         sg.key = key;
         sg.gen = workspace_generation(sl.ws);
         sg.graph = g;
         sg.exec = exec;
-        sg.arg_nodes = render_arg_nodes(g);
+        sg.arg_nodes = arg_nodes;
         sg.last_use = ++S->clock;
         if ((int)sl.graphs.size() >= kGraphsPerSlot) {   // evict the least recently used
             auto lru = std::min_element(sl.graphs.begin(), sl.graphs.end(),
