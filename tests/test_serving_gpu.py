@@ -141,3 +141,37 @@ def test_overflowing_request_is_rerun(env):
     finally:
         srv.close()
         r.unload_scene(h)
+
+
+def test_batched_raster_with_fp32_sum_tiles(env):
+    """Small views rasterised together by the persistent batched rasteriser,
+    one of them with a Gaussian whose Eq. 3 weight (exp(32)) sends its tiles
+    to the FP32 sums: every served image equals the view rendered alone."""
+    m, r, scenes = env
+    from paper_2603_11531_gb300.serving import Server
+    base = synth.uniform_scene(3000, seed=71).attrs
+    big = np.zeros((1, 24), np.float32)
+    big[0, 0:3] = (0.0, 0.0, -2.75)
+    big[0, 3:6] = (0.002, 0.002, 8.0)
+    big[0, 6] = 1.0
+    big[0, 10] = 0.9
+    big[0, 11:14] = 1.0
+    needle = synth.Scene(np.concatenate([base, big]).astype(np.float16))
+    hn = r.load_scene(needle)
+    cam_n = synth.look_at((0, 0, -3), (0, 0, 0), 320, 240, 60.0)
+    opts = m.render_opts()
+    reqs = [(hn, cam_n)] + [(scenes[k][1], cam) for k, cam in _requests(scenes, 5, seed=9)]
+    alone = [r.render(h, cam)["rgb"] for h, cam in reqs]
+    m.mgs_render(r.ws, hn, cam_n, opts, alone[0])
+    assert m.mgs_frame_stats(r.ws)["wide_tiles"] > 0
+    srv = Server(r.ctx, slots=6, max_batch=6, hbm_budget_bytes=2 << 30)
+    try:
+        outs = [torch.full((cam.height, cam.width, 3), float("nan"), device="cuda") for _, cam in reqs]
+        tickets = [srv.submit(h, cam, opts, o) for (h, cam), o in zip(reqs, outs)]
+        for t in tickets:
+            srv.wait(t)
+        for o, a in zip(outs, alone):
+            assert float((o - a).abs().max()) <= 1e-5
+    finally:
+        srv.close()
+        r.unload_scene(hn)
