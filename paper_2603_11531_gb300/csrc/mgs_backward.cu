@@ -90,18 +90,28 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(RenderArgs args,
     const float kq = -0.72134752044448170f;  // -log2(e) / 2
     float4(*wb)[32] = buf[warp];
 
+    // list entries two batches ahead, their records one batch ahead
+    uint32_t gid_n = 0, gid_nn = 0;
+    float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f), b_n = a_n, c_n = a_n;
+    if (start + lane < end) {
+        gid_n = __ldg(&args.gids[start + lane]);
+        a_n = __ldg(&args.rec[gid_n].a);
+        b_n = __ldg(&args.rec[gid_n].b);
+        c_n = __ldg(&args.rec[gid_n].c);
+    }
+    if (start + 32 + lane < end) gid_nn = __ldg(&args.gids[start + 32 + lane]);
     for (uint32_t base = start; base < end; base += 32) {
         const uint32_t j = base + lane;
-        bool cand = false;
-        uint32_t gid = 0;
-        float4 a, b, c;
-        if (j < end) {
-            gid = __ldg(&args.gids[j]);
-            a = __ldg(&args.rec[gid].a);
-            b = __ldg(&args.rec[gid].b);
-            c = __ldg(&args.rec[gid].c);
-            cand = block_may_hit(a.x, a.y, a.z, a.w, b.x, bx, by, 7.5f, 3.5f);
+        const uint32_t gid = gid_n;
+        const float4 a = a_n, b = b_n, c = c_n;
+        const bool cand = j < end && block_may_hit(a.x, a.y, a.z, a.w, b.x, bx, by, 7.5f, 3.5f);
+        if (j + 32 < end) {
+            gid_n = gid_nn;
+            a_n = __ldg(&args.rec[gid_n].a);
+            b_n = __ldg(&args.rec[gid_n].b);
+            c_n = __ldg(&args.rec[gid_n].c);
         }
+        if (j + 64 < end) gid_nn = __ldg(&args.gids[j + 64]);
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         if (cand) {
             const int pos = __popc(bal & ((1u << lane) - 1u));

@@ -142,24 +142,29 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
     int cnt[4] = {0, 0, 0, 0};
     ulonglong2(*wb)[32] = buf[warp];
 
+    // list entries two batches ahead, their records one batch ahead (the
+    // dependent record loads never wait on the list load)
     float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f), b_n = a_n, c_n = a_n;
+    uint32_t gid_nn = 0;
     if (start + lane < end) {
         const uint32_t gid = __ldg(&args.gids[start + lane]);
         a_n = __ldg(&args.rec[gid].a);
         b_n = __ldg(&args.rec[gid].b);
         c_n = __ldg(&args.rec[gid].c);
     }
+    if (start + 32 + lane < end) gid_nn = __ldg(&args.gids[start + 32 + lane]);
     for (uint32_t base = start; base < end; base += 32) {
         const uint32_t j = base + lane;
         const float4 a = a_n, b = b_n, c = c_n;
         const bool cand =
             j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bx, by, 7.5f, 3.5f));
         if (j + 32 < end) {
-            const uint32_t gid = __ldg(&args.gids[j + 32]);
+            const uint32_t gid = gid_nn;
             a_n = __ldg(&args.rec[gid].a);
             b_n = __ldg(&args.rec[gid].b);
             c_n = __ldg(&args.rec[gid].c);
         }
+        if (j + 64 < end) gid_nn = __ldg(&args.gids[j + 64]);
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         if (cand) {
             const int pos = __popc(bal & ((1u << lane) - 1u));
@@ -357,6 +362,9 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
     float2 b_n = make_float2(0.f, 0.f);
     uint4 w_n = make_uint4(0u, 0u, 0u, 0u);
     float d_n = 0.f;                      // depth image: -w d
+    // list entries are fetched two batches ahead and their records one batch
+    // ahead, so the dependent record loads never wait on the list load
+    uint32_t gid_nn = 0;
     if (start + lane < end) {
         const uint32_t gid = __ldg(&args.gids[start + lane]);
         a_n = __ldg(&args.rec[gid].a);
@@ -364,6 +372,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
         w_n = __ldg(&args.wt16[gid]);
         if constexpr (kDepth) d_n = __ldg(&args.rec[gid].c.w);
     }
+    if (start + 32 + lane < end) gid_nn = __ldg(&args.gids[start + 32 + lane]);
     for (uint32_t base = start; base < end; base += 32) {
         const uint32_t j = base + lane;
         const float4 a = a_n;
@@ -373,12 +382,13 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
         const bool cand =
             j < end && (no_cull || block_may_hit(a.x, a.y, a.z, a.w, b.x, bcx, bcy, 3.5f, 3.5f));
         if (j + 32 < end) {
-            const uint32_t gid = __ldg(&args.gids[j + 32]);
+            const uint32_t gid = gid_nn;
             a_n = __ldg(&args.rec[gid].a);
             b_n = __ldg(reinterpret_cast<const float2 *>(&args.rec[gid].b));
             w_n = __ldg(&args.wt16[gid]);
             if constexpr (kDepth) d_n = __ldg(&args.rec[gid].c.w);
         }
+        if (j + 64 < end) gid_nn = __ldg(&args.gids[j + 64]);
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         bool clamp = false;
         int pos = 0;
