@@ -70,25 +70,36 @@ __device__ __forceinline__ bool tile_may_hit(float mx, float my, float l11, floa
 // numbering of Gaussians [g0, g0 + 32) (one per lane; rectangle after
 // rectangle, row major inside each) whose tile passes tile_may_hit, 32 pairs
 // at a time over the warp's lanes; wide = the Gaussian carries kRectWide.
-template <class F>
-__device__ __forceinline__ void warp_pairs(const uint2 *__restrict__ rect,
-                                           const ProjRec *__restrict__ rec, int64_t n, int64_t g0,
-                                           int tiles_x, int pa, int pb, F &&f) {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = g0 + lane;
-    int x0 = 0, y0 = 0, w = 0, h = 0;
-    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
-    float gl22 = 0.f;
-    bool wide = false;
+// A lane's Gaussian of a group: rectangle and cull geometry, loaded together
+// (the geometry of a Gaussian without a rectangle is loaded but never used),
+// one group ahead of its use.
+struct GroupLoad {
+    uint2 r;
+    float4 a;
+    float l22;
+};
+__device__ __forceinline__ GroupLoad load_group(const uint2 *__restrict__ rect,
+                                                const ProjRec *__restrict__ rec, int64_t n,
+                                                int64_t g0) {
+    GroupLoad L{make_uint2(0u, 0u), make_float4(0.f, 0.f, 0.f, 0.f), 0.f};
+    const int64_t i = g0 + (threadIdx.x & 31);
     if (i < n) {
-        const uint2 r = rect[i];
-        rect_of(r, x0, y0, w, h);
-        wide = (r.y & kRectWide) != 0;
-        if (w > 0 && h > 0) {
-            ga = rec[i].a;
-            gl22 = rec[i].b.x;
-        }
+        L.r = __ldg(&rect[i]);
+        L.a = __ldg(&rec[i].a);
+        L.l22 = __ldg(&rec[i].b.x);
     }
+    return L;
+}
+
+template <class F>
+__device__ __forceinline__ void warp_pairs(const GroupLoad &L, int64_t g0, int tiles_x, int pa,
+                                           int pb, F &&f) {
+    const int lane = threadIdx.x & 31;
+    int x0 = 0, y0 = 0, w = 0, h = 0;
+    rect_of(L.r, x0, y0, w, h);
+    const bool wide = (L.r.y & kRectWide) != 0;
+    const float4 ga = L.a;
+    const float gl22 = L.l22;
     const int c = rect_pairs(w, h);
     const float winv = w > 0 ? 1.0f / (float)w : 0.0f;
     int incl = c;
@@ -167,15 +178,20 @@ __device__ __forceinline__ void warp_share_pairs(const uint2 *__restrict__ rect,
     if (c0 >= c1) return;
     int64_t g = find_group(cexcl, groups, c0);
     unsigned long long e0 = cexcl[g];
+    GroupLoad cur = load_group(rect, rec, n, g * 32);
     for (;;) {
         const unsigned long long e1 = cexcl[g + 1];
         const long long np = (long long)(e1 - e0) - kGroupCost;    // pairs of group g
         const long long pa = max(0ll, (long long)(c0 > e0 ? c0 - e0 : 0ull) - kGroupCost);
         const long long pb = min(np, (long long)(c1 - e0) - kGroupCost);
-        if (pa < pb) warp_pairs(rect, rec, n, g * 32, tiles_x, (int)pa, (int)pb, f);
-        if (c1 <= e1 || g + 1 >= groups) break;
+        const bool more = !(c1 <= e1 || g + 1 >= groups);
+        GroupLoad nxt{};
+        if (more) nxt = load_group(rect, rec, n, (g + 1) * 32);   // in flight meanwhile
+        if (pa < pb) warp_pairs(cur, g * 32, tiles_x, (int)pa, (int)pb, f);
+        if (!more) break;
         ++g;
         e0 = e1;
+        cur = nxt;
     }
 }
 
