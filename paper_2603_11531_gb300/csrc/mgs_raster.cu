@@ -3,19 +3,22 @@
 //   A = sum_i c_i a_i w_i,  B = sum_i a_i w_i,  T = prod_i (1 - a_i)
 //   C = (1 - T) A / B + T c_bg          (foreground term 0 when B = 0)
 //
-// One CTA per 16x16 tile, 64 threads, each thread owning four horizontally
-// adjacent pixels (two packed FP32x2 pairs).  Each warp owns a 16x8 block and
-// walks the tile's Gaussian list itself, testing each entry against its block
-// with a conservative bound and compacting (ballot) the candidates before
-// accumulating them in registers.  No atomics, no sort: every pixel is owned
-// by exactly one thread.
+// FP32 scenes (k_raster): one CTA per 16x16 tile, 64 threads, each thread
+// owning four horizontally adjacent pixels (two packed FP32x2 pairs).  Each
+// warp owns a 16x8 block and walks the tile's Gaussian list itself, testing
+// each entry against its block with a conservative bound (block_may_hit) and
+// compacting (ballot) the candidates before accumulating them in registers.
 //
-// FP16-attribute scenes take the sums A and B on the tensor cores instead
-// (raster_tile_tc below): alpha is still computed, tested and multiplied
-// into T in FP32 exactly as above, but a_i w_i c_i and a_i w_i are summed by
-// mma.sync (m16n8k16, FP16 operands, FP32 accumulation) with the weights split
+// FP16-attribute scenes (k_raster_tc): four warps of 8x8 pixels per tile;
+// alpha is still computed, tested and multiplied into T in FP32 exactly as
+// above, but a_i w_i c_i and a_i w_i are summed on the tensor cores by
+// mma.sync (m16n8k8, FP16 operands, FP32 accumulation) with the weights split
 // into FP16 high and low parts, which leaves alpha's FP16 rounding (relative
-// 2^-12 per term) as the only extra error.
+// 2^-12 per term) as the only extra error; tiles listing a Gaussian outside
+// the FP16 weight range take the FP32 code.
+//
+// No atomics, no sort: every pixel is owned by exactly one thread, and a
+// tile's list is accumulated in whatever order binning stored it.
 #include "mgs_internal.cuh"
 
 namespace mgs {
