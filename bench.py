@@ -283,7 +283,7 @@ def cpu_baseline_frame(pose: int = 0):
 
 
 # Kernels of this library one FP16 render launches: k_preprocess,
-# k_group_pairs, k_bin_plan, k_bin_count, k_scan_order, k_bin_scatter and
+# k_group_cost, k_bin_plan, k_bin_count, k_scan_order, k_bin_scatter and
 # k_raster_tc, once each (the tile-count memset is not a kernel).  The ncu
 # launch list of a bench run shows the same set per frame.
 KERNELS_PER_FRAME = 7
@@ -322,11 +322,12 @@ def run_reference(args):
 def _binning_bytes(n, visible, pairs):
     """Algorithmic DRAM bytes of the two list-building kernels per frame:
     the count reads every rectangle (8 B) and the cull geometry of the
-    visible Gaussians (20 B); the scatter reads the same, writes one 4-byte
-    list entry per listed pair and converts the visible Gaussians' weights
-    (reads 48-byte records, writes 16 B of FP16 weights)."""
+    visible Gaussians (20 B); the scatter reads the same and writes one
+    4-byte list entry per listed pair (preprocessing writes the FP16 weights;
+    the scatter rescales them only in frames whose largest weight needs it,
+    not on this view)."""
     count = 8 * n + 20 * visible
-    scatter = 8 * n + 20 * visible + 4 * pairs + 64 * visible
+    scatter = 8 * n + 20 * visible + 4 * pairs
     return count, scatter
 
 

@@ -4,26 +4,29 @@
 // (Sec. 2, Eq. 1 discussion; Sec. 3.1).  The lists built here are keyed by
 // tile only -- a counting sort by tile:
 //
-//   0. k_group_pairs, k_bin_plan: rectangle pair counts of every group of 32
-//      consecutive Gaussians and the exclusive scan of the group costs (pairs
-//      plus a fixed visit charge).  Every warp of the binning grid takes an
-//      equal contiguous share of that cost numbering, so neither a warp nor
-//      an SM waits on a few Gaussians that cover many tiles, nor on a long
-//      stretch of Gaussians that cover almost none.
-//   1. k_bin_count: each CTA counts the pairs of its warps' shares into a
-//      shared-memory histogram over the tiles; one global atomicAdd per (CTA,
-//      tile) reserves the CTA's block inside the tile and returns its base.
+//   0. k_group_cost, k_bin_plan: the plan cost of every group of 32
+//      consecutive Gaussians (its rectangle rows, each charged kRowCost plus
+//      the row's width in tiles) and the exclusive scan of the group costs
+//      plus a fixed visit charge.  Every warp of the binning grid takes an
+//      equal contiguous share of that cost numbering, cut at row boundaries.
+//   1. k_bin_count: each warp resolves its rows, 32 at a time (one per lane):
+//      the tiles of a rectangle row that pass the FP32 tile test form one
+//      interval (row_tiles), which is added to a per-CTA shared-memory
+//      difference array (+1 at its first tile, -1 after its last); a prefix
+//      sum per tile row turns those into the CTA's tile counts, and one
+//      global atomicAdd per (CTA, tile) reserves the CTA's block inside the
+//      tile and returns its base.
 //   2. k_scan_order: exclusive scan of the per-tile totals -> tile offsets,
 //      and the rasterisation order (longest lists first).
-//   3. k_bin_scatter: the same CTA re-expands the same pairs and places each
-//      one at offset[tile] + base[c][tile] + (shared-memory rank).
+//   3. k_bin_scatter: the same warps resolve the same rows again and write
+//      the rows' tiles, 32 (tile, Gaussian) pairs at a time over the warp, at
+//      offset[tile] + base[c][tile] + (shared-memory rank).
 //
-// Pairs are expanded warp-cooperatively: a group's 32 Gaussians are
-// flattened into one pair index space (prefix sum of rectangle areas) so a
-// Gaussian covering thousands of tiles does not serialise one lane.  A pair is listed
-// only if the FP32 tile test (tile_may_hit) allows an included pixel in the
-// tile; its rectangle alone (the 3-sigma bounding square) would list many
-// tiles a thin ellipse never reaches.  Order within a
+// A pair is listed only if the FP32 tile test (tile_may_hit) allows an
+// included pixel in the tile; its rectangle alone (the 3-sigma bounding
+// square) would list many tiles a thin ellipse never reaches.  Resolving a
+// row costs a handful of test evaluations instead of one per tile (the test
+// is monotone along the row up to its vertex, see row_tiles).  Order within a
 // tile follows the atomics and is not reproducible; the rasteriser does not
 // depend on it beyond FP32 rounding.
 #include "mgs_internal.cuh"
@@ -33,7 +36,7 @@ namespace {
 
 constexpr int kScanThreads = 1024;
 constexpr int kBinThreads = 1024;
-constexpr int kBand = 32768;          // tiles per shared-memory band (128 KB)
+constexpr int kBand = 32768;          // words per shared-memory band (128 KB)
 
 __device__ __forceinline__ void rect_of(const uint2 r, int &x0, int &y0, int &w, int &h) {
     x0 = r.x & 0xFFFF;
@@ -41,8 +44,6 @@ __device__ __forceinline__ void rect_of(const uint2 r, int &x0, int &y0, int &w,
     w = (int)(r.x >> 16) - x0;
     h = (int)((r.y & ~kRectWide) >> 16) - y0;
 }
-// Number of (tile, Gaussian) pairs of a rectangle.
-__device__ __forceinline__ int rect_pairs(int w, int h) { return w > 0 && h > 0 ? w * h : 0; }
 
 // FP32-contract tile test: may Gaussian (m, l) include a pixel centre of tile
 // (tx, ty)?  Slab bounds at the tile centre with half extent 7.5 and a 2^-18
@@ -66,10 +67,208 @@ __device__ __forceinline__ bool tile_may_hit(float mx, float my, float l11, floa
     return __fsub_rn(e1c, h1) <= __fadd_rn(3.0f, m1) && __fsub_rn(e2c, h2) <= __fadd_rn(3.0f, m2);
 }
 
-// Calls f(tile, gid, wide) for the pairs [pa, pb) of the flattened pair
-// numbering of Gaussians [g0, g0 + 32) (one per lane; rectangle after
-// rectangle, row major inside each) whose tile passes tile_may_hit, 32 pairs
-// at a time over the warp's lanes; wide = the Gaussian carries kRectWide.
+// Row constants of the FP32 tile test for one tile row of one Gaussian:
+// along the row only dxb = (tile centre x) - m_x changes.
+struct RowTest {
+    float mx, l11, P, h1, s12;   // P = l21 dyb, h1 = |l11| h + |l21| h, s12 = |l21| (|dyb| + h)
+};
+// e1c - h1 of tile tx (left-hand side of the test's first slab)
+__device__ __forceinline__ float row_lhs(const RowTest &r, int tx) {
+    const float dxb = __fsub_rn((float)(tx * kTile + 8), r.mx);
+    return __fsub_rn(fabsf(__fmaf_rn(r.l11, dxb, r.P)), r.h1);
+}
+// l11 dxb + P of tile tx (its sign changes once along the row)
+__device__ __forceinline__ float row_e1(const RowTest &r, int tx) {
+    return __fmaf_rn(r.l11, __fsub_rn((float)(tx * kTile + 8), r.mx), r.P);
+}
+// 3 + m1 for |dxb| = adx (right-hand side of the first slab)
+__device__ __forceinline__ float row_rhs(const RowTest &r, float adx) {
+    const float s1 = __fadd_rn(__fmul_rn(fabsf(r.l11), __fadd_rn(adx, 7.5f)), r.s12);
+    return __fadd_rn(3.0f, __fmul_rn(3.814697265625e-06f, __fadd_rn(s1, 4.0f)));
+}
+__device__ __forceinline__ int clamp_tile(float v, int lo, int hi) {
+    return (int)fminf(fmaxf(v, (float)lo), (float)hi);   // NaN -> lo
+}
+
+// Smallest t in [lo, hi] with row_lhs(t) <= K, starting from `guess`; the
+// predicate is false ... false true ... true on [lo, hi] and true at hi.
+// A few steps from a good guess, else bisection.  *v: row_lhs at the result.
+__device__ __forceinline__ int row_first(const RowTest &r, float K, int lo, int hi, int guess,
+                                         float &v) {
+    int t = min(max(guess, lo), hi);
+    v = row_lhs(r, t);
+    if (v <= K) {
+        for (int s = 0; s < 4 && t > lo; ++s) {
+            const float u = row_lhs(r, t - 1);
+            if (!(u <= K)) return t;
+            --t;
+            v = u;
+        }
+        if (t == lo) return t;
+        hi = t;
+    } else {
+        for (int s = 0; s < 4; ++s) {
+            ++t;
+            v = row_lhs(r, t);
+            if (v <= K) return t;
+        }
+        lo = t + 1;
+    }
+    while (lo < hi) {   // bisection on [lo, hi], predicate true at hi
+        const int m = (lo + hi) >> 1;
+        if (row_lhs(r, m) <= K) hi = m;
+        else lo = m + 1;
+    }
+    v = row_lhs(r, lo);
+    return lo;
+}
+// Largest t in [lo, hi] with row_lhs(t) <= K (true ... true false ... false,
+// true at lo).
+__device__ __forceinline__ int row_last(const RowTest &r, float K, int lo, int hi, int guess,
+                                        float &v) {
+    int t = min(max(guess, lo), hi);
+    v = row_lhs(r, t);
+    if (v <= K) {
+        for (int s = 0; s < 4 && t < hi; ++s) {
+            const float u = row_lhs(r, t + 1);
+            if (!(u <= K)) return t;
+            ++t;
+            v = u;
+        }
+        if (t == hi) return t;
+        lo = t;
+    } else {
+        for (int s = 0; s < 4; ++s) {
+            --t;
+            v = row_lhs(r, t);
+            if (v <= K) return t;
+        }
+        hi = t - 1;
+    }
+    while (lo < hi) {   // bisection on [lo, hi], predicate true at lo
+        const int m = (lo + hi + 1) >> 1;
+        if (row_lhs(r, m) <= K) lo = m;
+        else hi = m - 1;
+    }
+    v = row_lhs(r, lo);
+    return lo;
+}
+
+// The tiles of tile row ty inside rectangle columns [x0, x1) that pass
+// tile_may_hit, as one interval [a, b] (a > b: none).  Returns false when it
+// cannot establish that they form one interval; the caller then tests every
+// tile of the row.
+//
+// Why an interval: along the row the test is  |l11 dxb + P| - h1 <= 3 + m1
+// with dxb = fl(x - m_x).  Every operation is a correctly rounded, hence
+// monotone, function of its inputs, so fl(l11 dxb + P) is monotone in the
+// tile index, its absolute value falls and then rises, and for any fixed
+// bound K the tiles with  fl(|.| - h1) <= K  form an interval.  The margin m1
+// grows with |dxb| only, so on the rectangle it lies between its value at
+// |dxb| = 0 and its value at the farther end: the tiles passing with the
+// larger bound form an interval I_max, those passing with the smaller one an
+// interval I_min inside it, and only the tiles of I_max \ I_min (none in
+// practice: the bounds differ by 2^-18 relative) are tested one by one.  The
+// second slab |l22 dyb| - h2 <= 3 + m2 is the same for the whole row.
+__device__ __forceinline__ bool row_tiles(float mx, float my, float l11, float l21, float l22, int x0,
+                                       int x1, int ty, int &a, int &b) {
+    a = 1;
+    b = 0;
+    const float h = 7.5f;
+    const float dyb = __fsub_rn((float)(ty * kTile + 8), my);
+    const float u2 = __fadd_rn(fabsf(dyb), h);
+    const float e2c = fabsf(__fmul_rn(l22, dyb));
+    const float h2 = __fmul_rn(fabsf(l22), h);
+    const float m2 = __fmul_rn(3.814697265625e-06f, __fadd_rn(__fmul_rn(fabsf(l22), u2), 4.0f));
+    if (!(__fsub_rn(e2c, h2) <= __fadd_rn(3.0f, m2))) return true;   // no tile of the row
+    RowTest r;
+    r.mx = mx;
+    r.l11 = l11;
+    r.P = __fmul_rn(l21, dyb);
+    r.h1 = __fmaf_rn(fabsf(l11), h, __fmul_rn(fabsf(l21), h));
+    r.s12 = __fmul_rn(fabsf(l21), u2);
+    const int xl = x0, xr = x1 - 1;
+    if (!(fabsf(l11) > 0.0f && fabsf(l11) < 3.0e38f && fabsf(r.P) < 3.0e38f && fabsf(mx) < 3.0e38f))
+        return false;
+    const float Kmin = row_rhs(r, 0.0f);
+    const float Kmax = row_rhs(r, fmaxf(fabsf(__fsub_rn((float)(xl * kTile + 8), mx)),
+                                        fabsf(__fsub_rn((float)(xr * kTile + 8), mx))));
+    // vertex: the first tile t in [xl, xr + 1] at which l11 dxb + P has the
+    // sign of l11 (xr + 1 counts as such); |.| is smallest at t or t - 1
+    const float sg = l11 > 0.0f ? 1.0f : -1.0f;
+    const float tz = (mx - 8.0f - r.P / l11) * 0.0625f;
+    int t = clamp_tile(floorf(tz) + 1.0f, xl, xr + 1);
+    if (t <= xr && row_e1(r, t) * sg >= 0.0f) {
+        int s = 0;
+        while (t > xl && row_e1(r, t - 1) * sg >= 0.0f) {
+            --t;
+            if (++s > 8) return false;
+        }
+    } else {
+        int s = 0;
+        while (t <= xr && !(row_e1(r, t) * sg >= 0.0f)) {
+            ++t;
+            if (++s > 8) return false;
+        }
+    }
+    int tm;
+    float vm;
+    if (t > xr) {
+        tm = xr;
+        vm = row_lhs(r, xr);
+    } else if (t == xl) {
+        tm = xl;
+        vm = row_lhs(r, xl);
+    } else {
+        const float v1 = row_lhs(r, t), v0 = row_lhs(r, t - 1);
+        tm = v1 <= v0 ? t : t - 1;
+        vm = fminf(v1, v0);
+    }
+    if (!(vm <= Kmax)) return true;   // the lowest point fails even the larger bound
+    // I_max from guesses at the real crossings |l11 dxb + P| = h1 + Kmax
+    const float span = (r.h1 + Kmax) / fabsf(l11) * 0.0625f;
+    float va, vb;
+    const int a2 = row_first(r, Kmax, xl, tm, clamp_tile(floorf(tz - span) + 1.0f, xl, tm), va);
+    const int b2 = row_last(r, Kmax, tm, xr, clamp_tile(floorf(tz + span), tm, xr), vb);
+    if (va <= Kmin && vb <= Kmin) {   // I_min = I_max: every tile of [a2, b2] passes
+        a = a2;
+        b = b2;
+        return true;
+    }
+    // band tiles: test them one by one; together with I_min they must form one run
+    if (b2 - a2 > 64) return false;
+    int first = -1, last = -2, runs = 0;
+    bool prev = false;
+    for (int x = a2; x <= b2; ++x) {
+        const float v = row_lhs(r, x);
+        const bool p = v <= Kmin || (v <= Kmax && tile_may_hit(mx, my, l11, l21, l22, x, ty));
+        if (p && !prev) {
+            ++runs;
+            if (first < 0) first = x;
+        }
+        if (p) last = x;
+        prev = p;
+    }
+    if (runs > 1) return false;
+    if (runs == 1) {
+        a = first;
+        b = last;
+    }
+    return true;
+}
+
+// Plan cost of a rectangle row: kRowCost plus one unit per tile of the row.
+// The count resolves a row in about the same time whatever its width; the
+// scatter also writes the row's listed tiles (about 0.6 of its width).
+constexpr int kRowCost = 5;
+// Cost of a group in the work plan beyond its rows: a fixed charge for
+// visiting it (loading its 32 rectangles, the scans and the row split), so
+// that shares over sparse stretches of the scene (many Gaussians with one
+// or two rows each) stay short.  Measured on the 600k benchmark view: 512
+// balances the warps best among 32 ... 1024 (a visit costs about as much as
+// a hundred rows).
+constexpr int kGroupCost = 512;
+
 // A lane's Gaussian of a group: rectangle and cull geometry, loaded together
 // (the geometry of a Gaussian without a rectangle is loaded but never used),
 // one group ahead of its use.
@@ -91,17 +290,62 @@ __device__ __forceinline__ GroupLoad load_group(const uint2 *__restrict__ rect,
     return L;
 }
 
+// One row handed to a row callback: Gaussian gid, tile row ty, rectangle
+// columns [x0, x1), cull geometry, wide flag.
+struct RowItem {
+    uint32_t gid;
+    int ty, x0, x1;
+    float mx, my, l11, l21, l22;
+    bool wide;
+};
+
+// Rows wait in a per-warp queue in shared memory (kQueue slots)
+// until 32 of them fill a batch, so that sparse groups (a few visible
+// Gaussians with one or two rows) still give every lane a row.
+constexpr int kQueue = 64;
+
+// A queued row: {gid, ty | wide << 31, x0 | x1 << 16, l22} and {m_x, m_y, l11, l21}.
+struct RowSlot {
+    uint4 u;
+    float4 g;
+};
+
+// Calls f(active, item) with queued rows [qh, qh + cnt) (cnt <= 32), one per
+// lane; every lane calls f.
 template <class F>
-__device__ __forceinline__ void warp_pairs(const GroupLoad &L, int64_t g0, int tiles_x, int pa,
-                                           int pb, F &&f) {
+__device__ __forceinline__ void run_rows(const RowSlot *q, int qh, int cnt, F &&f) {
+    const int lane = threadIdx.x & 31;
+    RowItem it{};
+    const bool active = lane < cnt;
+    if (active) {
+        const RowSlot e = q[(qh + lane) & (kQueue - 1)];
+        it.gid = e.u.x;
+        it.ty = (int)(e.u.y & 0x7FFFFFFFu);
+        it.wide = (e.u.y >> 31) != 0u;
+        it.x0 = (int)(e.u.z & 0xFFFFu);
+        it.x1 = (int)(e.u.z >> 16);
+        it.l22 = __uint_as_float(e.u.w);
+        it.mx = e.g.x;
+        it.my = e.g.y;
+        it.l11 = e.g.z;
+        it.l21 = e.g.w;
+    }
+    f(active, it);
+}
+
+// Queues the rows of the group at g0 (Gaussians g0 .. g0 + 31, one per lane)
+// whose start cost lies in [ca, cb) of the group's row cost numbering
+// (Gaussian after Gaussian, rows top to bottom, row k of Gaussian i starting
+// at cost excl_i + k (kRowCost + w_i)), and runs every full batch of 32.
+template <class F>
+__device__ __forceinline__ void warp_rows(const GroupLoad &L, int64_t g0, int ca, int cb,
+                                          RowSlot *q, int &qh, int &qn, F &&f) {
     const int lane = threadIdx.x & 31;
     int x0 = 0, y0 = 0, w = 0, h = 0;
     rect_of(L.r, x0, y0, w, h);
     const bool wide = (L.r.y & kRectWide) != 0;
-    const float4 ga = L.a;
-    const float gl22 = L.l22;
-    const int c = rect_pairs(w, h);
-    const float winv = w > 0 ? 1.0f / (float)w : 0.0f;
+    const int rc = kRowCost + w;
+    const int c = (w > 0 && h > 0) ? h * rc : 0;
     int incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -109,45 +353,50 @@ __device__ __forceinline__ void warp_pairs(const GroupLoad &L, int64_t g0, int t
         if (lane >= o) incl += y;
     }
     const int excl = incl - c;
-    const int P = min(__shfl_sync(0xffffffffu, incl, 31), pb);
-    for (int base = pa; base < P; base += 32) {
+    // rows k with ca <= excl + k rc < cb
+    int r0 = 0, nr = 0;
+    if (c > 0) {
+        r0 = ca > excl ? (ca - excl + rc - 1) / rc : 0;
+        const int r1 = cb > excl ? min((cb - excl + rc - 1) / rc, h) : 0;
+        nr = max(r1 - r0, 0);
+    }
+    int rincl = nr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, rincl, o);
+        if (lane >= o) rincl += y;
+    }
+    const int rexcl = rincl - nr;
+    const int R = __shfl_sync(0xffffffffu, rincl, 31);
+    const int ybase = y0 + r0 - rexcl;   // row of index p for this lane: ybase + p
+    for (int base = 0; base < R; base += 32) {
         const int p = base + lane;
         // owner: the largest lane whose exclusive prefix is <= p
         int lo = 0;
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1) {
-            const int e = __shfl_sync(0xffffffffu, excl, lo + step);
+            const int e = __shfl_sync(0xffffffffu, rexcl, lo + step);
             if (e <= p) lo += step;
         }
-        const int ox0 = __shfl_sync(0xffffffffu, x0, lo);
-        const int oy0 = __shfl_sync(0xffffffffu, y0, lo);
-        const int ow = __shfl_sync(0xffffffffu, w, lo);
-        const float oinv = __shfl_sync(0xffffffffu, winv, lo);
-        const int oe = __shfl_sync(0xffffffffu, excl, lo);
-        const float mx = __shfl_sync(0xffffffffu, ga.x, lo);
-        const float my = __shfl_sync(0xffffffffu, ga.y, lo);
-        const float l11 = __shfl_sync(0xffffffffu, ga.z, lo);
-        const float l21 = __shfl_sync(0xffffffffu, ga.w, lo);
-        const float l22 = __shfl_sync(0xffffffffu, gl22, lo);
-        const bool owide = __shfl_sync(0xffffffffu, wide, lo);
-        if (p < P) {
-            const int k = p - oe;
-            // k / ow via the reciprocal, then corrected by one step either way
-            // (the product is off by at most 2^-23 (k + 0.5) / ow < 1 for any k < 2^23)
-            int ky = (int)(((float)k + 0.5f) * oinv);
-            if (ky * ow > k) --ky;
-            else if ((ky + 1) * ow <= k) ++ky;
-            const int tx = ox0 + (k - ky * ow), ty = oy0 + ky;
-            if (tile_may_hit(mx, my, l11, l21, l22, tx, ty))
-                f(ty * tiles_x + tx, (uint32_t)(g0 + lo), owide);
+        const int ty = __shfl_sync(0xffffffffu, ybase, lo) + p;
+        const uint32_t xw = __shfl_sync(0xffffffffu, (uint32_t)x0 | ((uint32_t)(x0 + w) << 16) |
+                                                         (wide ? 0x80000000u : 0u), lo);
+        RowSlot e;
+        e.u = make_uint4((uint32_t)(g0 + lo), (uint32_t)ty | (xw & 0x80000000u), xw & 0x7FFFFFFFu,
+                         __float_as_uint(__shfl_sync(0xffffffffu, L.l22, lo)));
+        e.g = make_float4(__shfl_sync(0xffffffffu, L.a.x, lo), __shfl_sync(0xffffffffu, L.a.y, lo),
+                          __shfl_sync(0xffffffffu, L.a.z, lo), __shfl_sync(0xffffffffu, L.a.w, lo));
+        if (p < R) q[(qh + qn + lane) & (kQueue - 1)] = e;
+        __syncwarp();
+        qn += min(32, R - base);
+        if (qn >= 32) {
+            run_rows(q, qh, 32, f);
+            qh = (qh + 32) & (kQueue - 1);
+            qn -= 32;
+            __syncwarp();
         }
     }
 }
-
-// Cost of a group in the work plan: its rectangle pairs plus a fixed charge
-// for visiting it (loading and scanning 32 rectangles), so that shares over
-// sparse stretches of the scene (many Gaussians, few pairs) stay short.
-constexpr int kGroupCost = 64;
 
 // Largest group g with cexcl[g] <= c (c < cexcl[groups]).
 __device__ __forceinline__ int64_t find_group(const unsigned long long *__restrict__ cexcl,
@@ -161,59 +410,78 @@ __device__ __forceinline__ int64_t find_group(const unsigned long long *__restri
     return lo;
 }
 
-// Calls f(tile, gid, wide) for the listed pairs of this warp's share of the work
-// plan: group g occupies costs [cexcl[g], cexcl[g + 1]), its visit charge
-// first and then one unit per rectangle pair in the group's pair numbering;
-// warp w of W takes costs [C w / W, C (w + 1) / W) of the total C.
+// Calls f(active, item) for the rows of this warp's share of the work plan:
+// group g occupies costs [cexcl[g], cexcl[g + 1]), its visit charge first and
+// then its row costs; warp w of W takes costs [C w / W, C (w + 1) / W) of the
+// total C, and a row belongs to the share holding its start cost.  The plan
+// entries are read 32 at a time and groups without rows (all Gaussians
+// culled) are skipped without loading them; each group with rows is loaded
+// while the previous one is processed.
 template <class F>
-__device__ __forceinline__ void warp_share_pairs(const uint2 *__restrict__ rect,
-                                                 const ProjRec *__restrict__ rec, int64_t n,
-                                                 const unsigned long long *__restrict__ cexcl,
-                                                 int64_t groups, int tiles_x, F &&f) {
+__device__ __forceinline__ void warp_share_rows(const uint2 *__restrict__ rect,
+                                                const ProjRec *__restrict__ rec, int64_t n,
+                                                const unsigned long long *__restrict__ cexcl,
+                                                int64_t groups, RowSlot *q, F &&f) {
     if (groups == 0) return;
+    const int lane = threadIdx.x & 31;
+    int qh = 0, qn = 0;   // queued rows: slots [qh, qh + qn) mod kQueue
     const unsigned long long C = cexcl[groups];
     const unsigned long long W = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     const unsigned long long w = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const unsigned long long c0 = C * w / W, c1 = C * (w + 1) / W;
     if (c0 >= c1) return;
-    int64_t g = find_group(cexcl, groups, c0);
-    unsigned long long e0 = cexcl[g];
-    GroupLoad cur = load_group(rect, rec, n, g * 32);
-    for (;;) {
-        const unsigned long long e1 = cexcl[g + 1];
-        const long long np = (long long)(e1 - e0) - kGroupCost;    // pairs of group g
-        const long long pa = max(0ll, (long long)(c0 > e0 ? c0 - e0 : 0ull) - kGroupCost);
-        const long long pb = min(np, (long long)(c1 - e0) - kGroupCost);
-        const bool more = !(c1 <= e1 || g + 1 >= groups);
-        GroupLoad nxt{};
-        if (more) nxt = load_group(rect, rec, n, (g + 1) * 32);   // in flight meanwhile
-        if (pa < pb) warp_pairs(cur, g * 32, tiles_x, (int)pa, (int)pb, f);
-        if (!more) break;
-        ++g;
-        e0 = e1;
-        cur = nxt;
+    for (int64_t gb = find_group(cexcl, groups, c0); gb < groups; gb += 32) {
+        const int64_t gl = gb + lane;
+        const unsigned long long e0l = gl < groups ? cexcl[gl] : C;
+        const unsigned long long e1l = gl < groups ? cexcl[gl + 1] : C;
+        // groups of this chunk with rows whose row costs meet [c0, c1)
+        unsigned m = __ballot_sync(0xffffffffu, gl < groups && e1l - e0l > (unsigned long long)kGroupCost &&
+                                                    e1l > c0 && e0l + kGroupCost < c1);
+        const bool done = __ballot_sync(0xffffffffu, gl >= groups || e1l >= c1) != 0u;
+        if (m) {
+            int j = __ffs(m) - 1;
+            m &= m - 1;
+            GroupLoad cur = load_group(rect, rec, n, (gb + j) * 32);
+            for (;;) {
+                const int jn = m ? __ffs(m) - 1 : -1;
+                GroupLoad nxt{};
+                if (jn >= 0) nxt = load_group(rect, rec, n, (gb + jn) * 32);   // in flight meanwhile
+                const unsigned long long e0 = __shfl_sync(0xffffffffu, e0l, j);
+                const unsigned long long e1 = __shfl_sync(0xffffffffu, e1l, j);
+                const long long nc = (long long)(e1 - e0) - kGroupCost;    // row costs of the group
+                const long long ca = max(0ll, (long long)(c0 > e0 ? c0 - e0 : 0ull) - kGroupCost);
+                const long long cb = min(nc, (long long)(c1 - e0) - kGroupCost);
+                if (ca < cb) warp_rows(cur, (gb + j) * 32, (int)ca, (int)cb, q, qh, qn, f);
+                if (jn < 0) break;
+                j = jn;
+                m &= m - 1;
+                cur = nxt;
+            }
+        }
+        if (done) break;
     }
+    if (qn > 0) run_rows(q, qh, qn, f);
 }
 
-// Rectangle pair count of every group of 32 consecutive Gaussians (one warp
-// per group).
-__global__ void __launch_bounds__(kBinThreads) k_group_pairs(const uint2 *__restrict__ rect,
-                                                             int64_t n, uint32_t *__restrict__ grp) {
+// Plan cost of every group of 32 consecutive Gaussians: the sum of
+// h (kRowCost + w) over its rectangles (one warp per group).
+__global__ void __launch_bounds__(kBinThreads) k_group_cost(const uint2 *__restrict__ rect,
+                                                            int64_t n, uint32_t *__restrict__ grp) {
     const int64_t g = ((int64_t)blockIdx.x * kBinThreads + threadIdx.x) >> 5;
     const int64_t i = g * 32 + (threadIdx.x & 31);
     uint32_t c = 0;
     if (i < n) {
         int x0, y0, w, h;
         rect_of(rect[i], x0, y0, w, h);
-        c = (uint32_t)rect_pairs(w, h);
+        c = (w > 0 && h > 0) ? (uint32_t)(h * (kRowCost + w)) : 0u;
     }
     c = __reduce_add_sync(0xffffffffu, c);
     if ((threadIdx.x & 31) == 0 && g * 32 < n) grp[g] = c;
 }
 
-// Exclusive scan of the group costs (pairs + kGroupCost) into
-// cexcl[0..groups] (64-bit), by one block, kPlanSeg groups at a time staged
-// in shared memory so that global loads and stores stay coalesced.
+// Exclusive scan of the group costs (plus kGroupCost) into cexcl[0..groups]
+// (64-bit), by one block, kPlanSeg groups at a time staged in shared memory
+// so that global loads and stores stay coalesced.
 constexpr int kPlanSeg = 16384;   // 64-bit costs per pass
 // Shared-memory slot of entry i: one pad word every 16 entries, so that
 // threads scanning runs of 16 consecutive entries hit different banks.
@@ -267,92 +535,157 @@ __global__ void __launch_bounds__(kScanThreads) k_bin_plan(const uint32_t *__res
     if (tid == 0) cexcl[groups] = carry;
 }
 
+// Tile rows per shared-memory band: the count's difference array takes
+// tiles_x + 1 words per tile row.
+__host__ __device__ __forceinline__ int band_rows(int tiles_x, int tiles_y) {
+    const int r = kBand / (tiles_x + 1);
+    return r < tiles_y ? r : tiles_y;
+}
+
 // Counts per tile; with `tc` (tensor-core rasteriser) and a frame that has
 // wide Gaussians, also sets kTileWide in tile_count[] of every tile that
 // lists one (per-CTA counts stay below 2^31, so the flag never meets a carry).
+// Shared memory: the band's difference array (band_rows x (tiles_x + 1)
+// ints), then one wide-flag byte per tile of the band.
 __global__ void __launch_bounds__(kBinThreads, 1) k_bin_count(const uint2 *__restrict__ rect,
                                                            const ProjRec *__restrict__ rec,
-                                                           int64_t n, int tiles_x, int T,
+                                                           int64_t n, int tiles_x, int tiles_y,
                                                            const unsigned long long *__restrict__ excl,
                                                            int64_t groups,
                                                            uint32_t *__restrict__ tile_count,
                                                            uint32_t *__restrict__ bases,
                                                            const DevStatus *__restrict__ status,
                                                            bool tc) {
-    extern __shared__ uint32_t cnt_s[];
+    extern __shared__ int diff_s[];
+    __shared__ RowSlot queue_s[kBinThreads / 32][kQueue];
+    const int T = tiles_x * tiles_y;
+    const int stride = tiles_x + 1;
+    const int brows = band_rows(tiles_x, tiles_y);
+    unsigned char *wide_s = reinterpret_cast<unsigned char *>(diff_s + brows * stride);
     const bool mark = tc && status->wide_bits != 0u;
-    for (int band0 = 0; band0 < T; band0 += kBand) {
-        const int bn = min(kBand, T - band0);
-        for (int t = threadIdx.x; t < bn; t += blockDim.x) cnt_s[t] = 0u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int ty0 = 0; ty0 < tiles_y; ty0 += brows) {
+        const int nrows = min(brows, tiles_y - ty0);
+        for (int i = threadIdx.x; i < nrows * stride; i += kBinThreads) diff_s[i] = 0;
+        if (mark)
+            for (int i = threadIdx.x; i < nrows * tiles_x; i += kBinThreads) wide_s[i] = 0;
         __syncthreads();
-        warp_share_pairs(rect, rec, n, excl, groups, tiles_x, [&](int tile, uint32_t, bool wide) {
-            const int t = tile - band0;
-            if ((unsigned)t < (unsigned)bn) {
-                atomicAdd(&cnt_s[t], 1u);
-                if (mark && wide) atomicOr(&cnt_s[t], kTileWide);
+        warp_share_rows(rect, rec, n, excl, groups, queue_s[warp], [&](bool active, const RowItem &it) {
+            const int ry = it.ty - ty0;
+            if (!active || (unsigned)ry >= (unsigned)nrows) return;
+            int *d = diff_s + ry * stride;
+            int a, b;
+            if (row_tiles(it.mx, it.my, it.l11, it.l21, it.l22, it.x0, it.x1, it.ty, a, b)) {
+                if (a <= b) {
+                    atomicAdd(&d[a], 1);
+                    atomicAdd(&d[b + 1], -1);
+                    if (mark && it.wide)
+                        for (int x = a; x <= b; ++x) wide_s[ry * tiles_x + x] = 1;
+                }
+            } else {   // not one interval: every tile of the row on its own
+                for (int x = it.x0; x < it.x1; ++x)
+                    if (tile_may_hit(it.mx, it.my, it.l11, it.l21, it.l22, x, it.ty)) {
+                        atomicAdd(&d[x], 1);
+                        atomicAdd(&d[x + 1], -1);
+                        if (mark && it.wide) wide_s[ry * tiles_x + x] = 1;
+                    }
             }
         });
         __syncthreads();
-        for (int t = threadIdx.x; t < bn; t += blockDim.x) {
-            const uint32_t v = cnt_s[t];
-            const uint32_t c = v & kTileMask;
-            if (c)
-                bases[(int64_t)blockIdx.x * T + band0 + t] =
-                    atomicAdd(&tile_count[band0 + t], c) & kTileMask;
-            if (v & kTileWide) atomicOr(&tile_count[band0 + t], kTileWide);
+        // prefix sums along each tile row -> this CTA's tile counts; reserve
+        // the CTA's block in every tile it lists pairs in
+        for (int ry = warp; ry < nrows; ry += kBinThreads / 32) {
+            int carry = 0;
+            for (int xb = 0; xb < tiles_x; xb += 32) {
+                const int x = xb + lane;
+                int v = x < tiles_x ? diff_s[ry * stride + x] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += y;
+                }
+                const int c = carry + v;
+                carry += __shfl_sync(0xffffffffu, v, 31);
+                if (x < tiles_x) {
+                    const int t = (ty0 + ry) * tiles_x + x;
+                    if (c > 0)
+                        bases[(int64_t)blockIdx.x * T + t] =
+                            atomicAdd(&tile_count[t], (uint32_t)c) & kTileMask;
+                    if (mark && wide_s[ry * tiles_x + x]) atomicOr(&tile_count[t], kTileWide);
+                }
+            }
         }
         __syncthreads();
     }
 }
 
-// Tensor-core weights of Gaussian g: (w c_r, w c_g, w c_b, w) times the
-// frame's power-of-two scale (2^(14 - e) when the largest weight has
-// exponent e >= 14), as FP16 high parts then FP16 low parts.
-__device__ __forceinline__ uint4 weights_f16(const ProjRec &r, float scale) {
-    const float w[4] = {-r.b.w * scale, -r.c.x * scale, -r.c.y * scale, -r.b.z * scale};
-    __half hi[4], lo[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        hi[k] = __float2half_rn(w[k]);
-        lo[k] = __float2half_rn(w[k] - __half2float(hi[k]));
-    }
-    uint4 u;
-    u.x = (uint32_t)__half_as_ushort(hi[0]) | ((uint32_t)__half_as_ushort(hi[1]) << 16);
-    u.y = (uint32_t)__half_as_ushort(hi[2]) | ((uint32_t)__half_as_ushort(hi[3]) << 16);
-    u.z = (uint32_t)__half_as_ushort(lo[0]) | ((uint32_t)__half_as_ushort(lo[1]) << 16);
-    u.w = (uint32_t)__half_as_ushort(lo[2]) | ((uint32_t)__half_as_ushort(lo[3]) << 16);
-    return u;
-}
-
 __global__ void __launch_bounds__(kBinThreads, 1) k_bin_scatter(
-    const uint2 *__restrict__ rect, int64_t n, int tiles_x, int T,
+    const uint2 *__restrict__ rect, int64_t n, int tiles_x, int tiles_y,
     const unsigned long long *__restrict__ excl, int64_t groups,
     const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ bases,
     uint32_t *__restrict__ gids, uint64_t capacity, const DevStatus *__restrict__ status,
     const ProjRec *__restrict__ rec, uint4 *__restrict__ wt16) {
     extern __shared__ uint32_t cur_s[];
+    __shared__ RowSlot queue_s[kBinThreads / 32][kQueue];
     if (status->last_pairs > capacity) return;  // overflow: lists are not built
-    if (wt16) {   // tensor-core rasteriser: FP16 weights of the visible Gaussians
-        const int we = (int)((status->wmax_frame_bits >> 23) & 0xFFu) - 127;
-        const float scale = we >= 14 ? __int_as_float((127 + 14 - we) << 23) : 1.0f;
+    const int we = (int)((status->wmax_frame_bits >> 23) & 0xFFu) - 127;
+    if (wt16 && we >= 14) {   // preprocessing wrote the FP16 weights unscaled; rescale them
+        const float scale = __int_as_float((127 + 14 - we) << 23);
         for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
              g += (int64_t)gridDim.x * blockDim.x) {
             const uint2 r = rect[g];
             if (r.x | r.y) wt16[g] = weights_f16(rec[g], scale);
         }
     }
-    for (int band0 = 0; band0 < T; band0 += kBand) {
-        const int bn = min(kBand, T - band0);
+    const int T = tiles_x * tiles_y;
+    const int brows = band_rows(tiles_x, tiles_y);
+    const int lane = threadIdx.x & 31;
+    for (int ty0 = 0; ty0 < tiles_y; ty0 += brows) {
+        const int nrows = min(brows, tiles_y - ty0);
+        const int t0 = ty0 * tiles_x, bn = nrows * tiles_x;
         // entries of tiles this CTA has no pairs in are never read
-        for (int t = threadIdx.x; t < bn; t += blockDim.x)
-            cur_s[t] = offsets[band0 + t] + bases[(int64_t)blockIdx.x * T + band0 + t];
+        for (int i = threadIdx.x; i < bn; i += kBinThreads)
+            cur_s[i] = offsets[t0 + i] + bases[(int64_t)blockIdx.x * T + t0 + i];
         __syncthreads();
-        warp_share_pairs(rect, rec, n, excl, groups, tiles_x, [&](int tile, uint32_t gid, bool) {
-            const int t = tile - band0;
-            if ((unsigned)t < (unsigned)bn) {
-                const uint32_t slot = atomicAdd(&cur_s[t], 1u);
-                if (slot < capacity) gids[slot] = gid;
+        warp_share_rows(rect, rec, n, excl, groups, queue_s[threadIdx.x >> 5], [&](bool active, const RowItem &it) {
+            const int ry = it.ty - ty0;
+            const bool in = active && (unsigned)ry < (unsigned)nrows;
+            int a = 1, b = 0;
+            const bool one = in ? row_tiles(it.mx, it.my, it.l11, it.l21, it.l22, it.x0, it.x1,
+                                            it.ty, a, b)
+                                : true;
+            // the rows' tiles, 32 pairs at a time over the warp
+            const int L = (in && one && a <= b) ? b - a + 1 : 0;
+            int incl = L;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
+            const int ex = incl - L;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int tb = ry * tiles_x + a - ex;   // band tile of pair p of this lane: tb + p
+            for (int base = 0; base < total; base += 32) {
+                const int p = base + lane;
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int e = __shfl_sync(0xffffffffu, ex, lo + step);
+                    if (e <= p) lo += step;
+                }
+                const int t = __shfl_sync(0xffffffffu, tb, lo) + p;
+                const uint32_t gid = __shfl_sync(0xffffffffu, it.gid, lo);
+                if (p < total) {
+                    const uint32_t slot = atomicAdd(&cur_s[t], 1u);
+                    if (slot < capacity) gids[slot] = gid;
+                }
+            }
+            if (in && !one)   // not one interval: every tile of the row on its own
+                for (int x = it.x0; x < it.x1; ++x)
+                    if (tile_may_hit(it.mx, it.my, it.l11, it.l21, it.l22, x, it.ty)) {
+                        const uint32_t slot = atomicAdd(&cur_s[ry * tiles_x + x], 1u);
+                        if (slot < capacity) gids[slot] = it.gid;
+                    }
         });
         __syncthreads();
     }
@@ -464,25 +797,28 @@ int64_t bin_scratch_words(int64_t n, int64_t T, int sm_count) {
 
 cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch,
                            cudaStream_t stream, const cudaEvent_t *marks) {
-    const int T = a.cam.tiles_x * a.cam.tiles_y;
+    const int tx = a.cam.tiles_x, ty = a.cam.tiles_y;
+    const int T = tx * ty;
     const int C = bin_ctas(a.n, sm_count);
     const int64_t groups = (a.n + 31) / 32;
     uint32_t *bases = scratch;
     unsigned long long *excl =
         reinterpret_cast<unsigned long long *>(scratch + ((int64_t)C * T + 1) / 2 * 2);
     uint32_t *grp = reinterpret_cast<uint32_t *>(excl + groups + 1);
-    const size_t smem = (size_t)(T < kBand ? T : kBand) * sizeof(uint32_t);
+    const int brows = band_rows(tx, ty);
+    const size_t count_smem = ((size_t)brows * (tx + 1) * sizeof(int) + (size_t)brows * tx + 15) / 16 * 16;
+    const size_t scatter_smem = (size_t)brows * tx * sizeof(uint32_t);
     cudaError_t e = cudaMemsetAsync(a.tile_count, 0, (size_t)T * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
     if (a.n > 0) {
         if ((e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(kBand * sizeof(uint32_t)))) != cudaSuccess)
+                                      (int)(kBand * (sizeof(int) + 1)))) != cudaSuccess)
             return e;
         if ((e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(kBand * sizeof(uint32_t)))) != cudaSuccess)
             return e;
-        k_group_pairs<<<(int)((groups * 32 + kBinThreads - 1) / kBinThreads), kBinThreads, 0,
-                        stream>>>(a.rect, a.n, grp);
+        k_group_cost<<<(int)((groups * 32 + kBinThreads - 1) / kBinThreads), kBinThreads, 0,
+                       stream>>>(a.rect, a.n, grp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int plan_n = (int)(groups < kPlanSeg ? groups : kPlanSeg);
         const size_t plan_smem = (size_t)(plan_n + plan_n / 16) * sizeof(unsigned long long);
@@ -492,9 +828,9 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch,
         k_bin_plan<<<1, kScanThreads, plan_smem, stream>>>(grp, groups, excl);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (marks && (e = cudaEventRecord(marks[0], stream)) != cudaSuccess) return e;
-        k_bin_count<<<C, kBinThreads, smem, stream>>>(a.rect, a.rec, a.n, a.cam.tiles_x, T, excl,
-                                                      groups, a.tile_count, bases, a.status,
-                                                      tc_raster(a));
+        k_bin_count<<<C, kBinThreads, count_smem, stream>>>(a.rect, a.rec, a.n, tx, ty, excl, groups,
+                                                            a.tile_count, bases, a.status,
+                                                            tc_raster(a));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (marks && (e = cudaEventRecord(marks[1], stream)) != cudaSuccess) return e;
     } else if (marks) {
@@ -506,9 +842,10 @@ cudaError_t launch_binning(const RenderArgs &a, int sm_count, uint32_t *scratch,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (marks && (e = cudaEventRecord(marks[2], stream)) != cudaSuccess) return e;
     if (a.n == 0) return e;
-    k_bin_scatter<<<C, kBinThreads, smem, stream>>>(a.rect, a.n, a.cam.tiles_x, T, excl, groups,
-                                                    a.tile_offsets, bases, a.gids, a.capacity,
-                                                    a.status, a.rec, tc_raster(a) ? a.wt16 : nullptr);
+    k_bin_scatter<<<C, kBinThreads, scatter_smem, stream>>>(a.rect, a.n, tx, ty, excl, groups,
+                                                            a.tile_offsets, bases, a.gids,
+                                                            a.capacity, a.status, a.rec,
+                                                            tc_raster(a) ? a.wt16 : nullptr);
     return cudaGetLastError();
 }
 

@@ -161,13 +161,33 @@ struct RenderArgs {
 };
 
 // Does this render rasterise with tensor-core sums (FP16 attributes, no
-// comparator, not forced onto the FMA pipe)?  Binning then also converts
-// every visible Gaussian's weights to FP16 (args.wt16).  A depth image
+// comparator, not forced onto the FMA pipe)?  Preprocessing then also writes
+// every visible Gaussian's weights in FP16 (args.wt16; binning rescales them
+// when the frame's largest weight needs it).  A depth image
 // rendered this way takes its numerator sum d a w in FP32 and its
 // denominator from the tensor-core B.
 __host__ __device__ inline bool tc_raster(const RenderArgs &a) {
     return a.precision == MGS_PREC_FP16 &&
            (a.flags & (MGS_FLAG_RASTER_FMA | MGS_FLAG_SORTED)) == 0;
+}
+
+// Tensor-core weights of Gaussian g: (w c_r, w c_g, w c_b, w) times the
+// frame's power-of-two scale (2^(14 - e) when the largest weight has
+// exponent e >= 14), as FP16 high parts then FP16 low parts.
+__device__ __forceinline__ uint4 weights_f16(const ProjRec &r, float scale) {
+    const float w[4] = {-r.b.w * scale, -r.c.x * scale, -r.c.y * scale, -r.b.z * scale};
+    __half hi[4], lo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        hi[k] = __float2half_rn(w[k]);
+        lo[k] = __float2half_rn(w[k] - __half2float(hi[k]));
+    }
+    uint4 u;
+    u.x = (uint32_t)__half_as_ushort(hi[0]) | ((uint32_t)__half_as_ushort(hi[1]) << 16);
+    u.y = (uint32_t)__half_as_ushort(hi[2]) | ((uint32_t)__half_as_ushort(hi[3]) << 16);
+    u.z = (uint32_t)__half_as_ushort(lo[0]) | ((uint32_t)__half_as_ushort(lo[1]) << 16);
+    u.w = (uint32_t)__half_as_ushort(lo[2]) | ((uint32_t)__half_as_ushort(lo[3]) << 16);
+    return u;
 }
 
 // Can Gaussian (m, l) include any pixel centre of the block centred at (bx, by)

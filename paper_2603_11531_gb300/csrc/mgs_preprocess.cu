@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kWide ? tcw::kThreads : (kTC ? tc::kThreads : 
     tc::Smem &tsm = *reinterpret_cast<tc::Smem *>(smem_raw);
     const DevCamera &cam = args.cam;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool tc = args.wt16 != nullptr && tc_raster(args);
     uint32_t tc_phase = 0;
     bool tc_ok = true;
     WideLayout wl{};
@@ -295,6 +296,7 @@ __global__ void __launch_bounds__(kWide ? tcw::kThreads : (kTC ? tc::kThreads : 
         r.b = make_float4(c.l22, __log2f(opa), -w, -w * rgb[0]);
         r.c = make_float4(-w * rgb[1], -w * rgb[2], c.tz, -w * c.tz);
         args.rec[i] = r;
+        if (kFP16 && tc) args.wt16[i] = weights_f16(r, 1.0f);   // rescaled by binning if needed
         // weights outside the range of the FP16 tensor-core sums
         const float wm = w * fmaxf(fmaxf(1.0f, rgb[0]), fmaxf(rgb[1], rgb[2]));
         const bool wide = !(w >= 1.0f && wm < kWideWeight);

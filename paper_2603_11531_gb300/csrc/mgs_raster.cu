@@ -233,10 +233,10 @@ __device__ __forceinline__ void raster_tile(const RenderArgs &args, int tile,
 // FP32x2 operation serves both, and the packed pair of alphas is exactly the
 // A fragment the lane holds.  B = the chunk's weights [w c_r, w c_g, w c_b, w]
 // as FP16 high parts (columns 0-3) and low parts (columns 4-7), so column c +
-// column c + 4 is the sum with a 22-bit weight; binning prepares these FP16
-// weights once per Gaussian (k_bin_scatter), scaled by a power of two when
-// the frame's largest weight would overflow FP16 (the scale cancels in A / B
-// and is divided out here).  T stays in FP32 FMAs.  Tiles listing a Gaussian
+// column c + 4 is the sum with a 22-bit weight; preprocessing writes these
+// FP16 weights once per Gaussian, and binning rescales them by a power of two
+// when the frame's largest weight would overflow FP16 (the scale cancels in
+// A / B and is divided out here).  T stays in FP32 FMAs.  Tiles listing a Gaussian
 // outside that scale's range (kTileWide) are rasterised by the FMA tile code.
 constexpr int kTcThreads = 128;
 constexpr int kTcWarps = kTcThreads / 32;
@@ -408,7 +408,7 @@ __device__ __forceinline__ void raster_tile_tc(const RenderArgs &args, int tile,
             q[o] = b.x;
             q[2 + o] = b.y;
             clamp = b.y > kLogClamp;
-            wt[pos] = wv;                        // FP16 weights prepared during binning
+            wt[pos] = wv;                        // FP16 weights written by preprocessing
             if constexpr (kDepth) reinterpret_cast<float *>(&wd[pos >> 1])[o] = -dv;
         }
         // slots of this batch that need the 0.99 clamp

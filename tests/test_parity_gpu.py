@@ -309,9 +309,10 @@ def test_binning_work_plan_cases(R):
 
 @pytest.mark.parametrize("prec,use_mlp,tol", [("fp32", False, TOL_FP32), ("fp16", True, TOL_FP16_MLP)])
 def test_two_tile_bands(R, prec, use_mlp, tol):
-    """4096x2304 has 36,864 tiles, more than one shared-memory band of the
-    binning histograms (32,768 tiles): both bands hold listed pairs (means
-    spread over [-3, 3]^3 reach the bottom tile rows)."""
+    """4096x2304 has 256 x 144 tiles, more than one shared-memory band of
+    the binning (32,768 words: 127 tile rows of 257 difference-array words at
+    this width): both bands hold listed pairs (means spread over [-3, 3]^3
+    reach the bottom tile rows)."""
     sc = synth.uniform_scene(3000, seed=61, precision=prec)
     a = sc.attrs.copy()
     a[:, 0:3] *= 3.0
@@ -319,6 +320,46 @@ def test_two_tile_bands(R, prec, use_mlp, tol):
     scene.mlp = synth.random_mlp(62)
     cam = synth.look_at((0, 0, -10), (0, 0, 0), 4096, 2304, 60.0)
     out, ref = _render_both(R, scene, cam, use_mlp=use_mlp, bg=(0.1, 0.2, 0.3))
-    assert int(ref["offsets"][-1] - ref["offsets"][32768]) > 0
+    assert int(ref["offsets"][-1] - ref["offsets"][127 * 256]) > 0
     np.testing.assert_array_equal(out["count"], ref["count"])
+    assert np.abs(out["rgb"] - ref["rgb"]).max() <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_row_resolution_anisotropic(R, prec):
+    """Binning resolves each rectangle row of a Gaussian from a few
+    evaluations of the FP32 tile test (the passing tiles of a row form one
+    interval), not one test per tile.  Stress it with needle-thin ellipses
+    at every angle (a few pixels wide, hundreds long), Gaussians whose means
+    lie far outside the image, image-sized ones and tiny ones, at an odd
+    resolution: the lists must equal the oracle's per-tile lists as sets,
+    and the per-pixel counts must agree."""
+    rng = np.random.default_rng(71)
+    n = 3000
+    a = synth.uniform_scene(n, seed=72, precision="fp32").attrs.astype(np.float64)
+    kind = rng.integers(0, 4, n)
+    s = a[:, 3:6]
+    # needles: one long axis, two very short ones
+    nd = kind == 0
+    s[nd, 0] = np.exp(rng.uniform(-1.5, 0.5, nd.sum()))
+    s[nd, 1] = np.exp(rng.uniform(-8.0, -5.0, nd.sum()))
+    s[nd, 2] = np.exp(rng.uniform(-8.0, -5.0, nd.sum()))
+    # flat discs seen at grazing angles
+    fl = kind == 1
+    s[fl, 0:2] = np.exp(rng.uniform(-2.0, -0.5, (fl.sum(), 2)))
+    s[fl, 2] = 1e-4
+    # means far outside the frustum's centre, large enough to reach the image
+    far = kind == 2
+    a[far, 0:2] = rng.uniform(-4.0, 4.0, (far.sum(), 2))
+    s[far, :] = np.exp(rng.uniform(-1.0, 0.3, (far.sum(), 3)))
+    # tiny ones
+    ti = kind == 3
+    s[ti, :] = np.exp(rng.uniform(-7.0, -5.0, (ti.sum(), 3)))
+    a[:, 3:6] = s
+    scene = synth.Scene(a.astype(np.float32 if prec == "fp32" else np.float16))
+    cam = synth.look_at((0.3, -0.2, -3.2), (0, 0, 0), 1013, 771, 70.0)
+    out, ref = _render_both(R, scene, cam, bg=(0.1, 0.2, 0.3))
+    assert int(ref["offsets"][-1]) > 500_000
+    np.testing.assert_array_equal(out["count"], ref["count"])
+    tol = TOL_FP32 if prec == "fp32" else TOL_FP16_MLP
     assert np.abs(out["rgb"] - ref["rgb"]).max() <= tol
