@@ -18,9 +18,10 @@
 //      tile and returns its base.
 //   2. k_scan_order: exclusive scan of the per-tile totals -> tile offsets,
 //      and the rasterisation order (longest lists first).
-//   3. k_bin_scatter: the same warps resolve the same rows again, and each
-//      lane writes its row's tiles at offset[tile] + base[c][tile] +
-//      (shared-memory rank).
+//   3. k_bin_scatter: the same warps resolve the same rows again and write
+//      the rows' tiles (lane by lane, or spread over the warp when a batch
+//      holds a long row) at offset[tile] + base[c][tile] + (shared-memory
+//      rank).
 //
 // A pair is listed only if the FP32 tile test (tile_may_hit) allows an
 // included pixel in the tile; its rectangle alone (the 3-sigma bounding
@@ -619,6 +620,10 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_count(const uint2 *__res
     }
 }
 
+// Rows of at most this many listed tiles are written lane by lane; a batch
+// holding a longer one spreads its tiles over the warp instead.
+constexpr int kLaneRun = 16;
+
 __global__ void __launch_bounds__(kBinThreads, 1) k_bin_scatter(
     const uint2 *__restrict__ rect, int64_t n, int tiles_x, int tiles_y,
     const unsigned long long *__restrict__ excl, int64_t groups,
@@ -654,12 +659,38 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_scatter(
             const bool one = in ? row_tiles(it.mx, it.my, it.l11, it.l21, it.l22, it.x0, it.x1,
                                             it.ty, a, b)
                                 : true;
-            // each lane writes its own row's tiles
-            if (in && one) {
-                const int tb = ry * tiles_x;
-                for (int x = a; x <= b; ++x) {
-                    const uint32_t slot = atomicAdd(&cur_s[tb + x], 1u);
+            const int L = (in && one && a <= b) ? b - a + 1 : 0;
+            if (__reduce_max_sync(0xffffffffu, (unsigned)L) <= (unsigned)kLaneRun) {
+                // short rows: each lane writes its own row's tiles
+                for (int x = a; x < a + L; ++x) {
+                    const uint32_t slot = atomicAdd(&cur_s[ry * tiles_x + x], 1u);
                     if (slot < capacity) gids[slot] = it.gid;
+                }
+            } else {
+                // a long row among them: the rows' tiles, 32 at a time over the warp
+                int incl = L;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int ex = incl - L;
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                const int tb = ry * tiles_x + a - ex;   // band tile of pair p of this lane: tb + p
+                for (int base = 0; base < total; base += 32) {
+                    const int p = base + lane;
+                    int lo = 0;   // owner: the largest lane whose exclusive prefix is <= p
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int e = __shfl_sync(0xffffffffu, ex, lo + step);
+                        if (e <= p) lo += step;
+                    }
+                    const int t = __shfl_sync(0xffffffffu, tb, lo) + p;
+                    const uint32_t gid = __shfl_sync(0xffffffffu, it.gid, lo);
+                    if (p < total) {
+                        const uint32_t slot = atomicAdd(&cur_s[t], 1u);
+                        if (slot < capacity) gids[slot] = gid;
+                    }
                 }
             }
             if (in && !one)   // not one interval: every tile of the row on its own
