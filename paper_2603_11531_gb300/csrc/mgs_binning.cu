@@ -177,6 +177,9 @@ __device__ __forceinline__ int row_last(const RowTest &r, float K, int lo, int h
 // interval I_min inside it, and only the tiles of I_max \ I_min (none in
 // practice: the bounds differ by 2^-18 relative) are tested one by one.  The
 // second slab |l22 dyb| - h2 <= 3 + m2 is the same for the whole row.
+// Most rows are settled by a certificate: the two tiles nearest the real
+// crossings pass with the smaller bound and their outer neighbours fail with
+// the larger one, so I_min = I_max = the tiles between them.
 __device__ __forceinline__ bool row_tiles(float mx, float my, float l11, float l21, float l22, int x0,
                                        int x1, int ty, int &a, int &b) {
     a = 1;
@@ -200,10 +203,27 @@ __device__ __forceinline__ bool row_tiles(float mx, float my, float l11, float l
     const float Kmin = row_rhs(r, 0.0f);
     const float Kmax = row_rhs(r, fmaxf(fabsf(__fsub_rn((float)(xl * kTile + 8), mx)),
                                         fabsf(__fsub_rn((float)(xr * kTile + 8), mx))));
+    // real-valued crossings |l11 dxb + P| = h1 + Kmax around the vertex tz
+    const float tz = (mx - 8.0f - r.P / l11) * 0.0625f;
+    const float span = (r.h1 + Kmax) / fabsf(l11) * 0.0625f;
+    {   // fast path: the tiles gl, gr pass and their outer neighbours fail, so
+        // (I_max being an interval) I_max = [gl, gr]
+        const int gl = clamp_tile(floorf(tz - span) + 1.0f, xl, xr);
+        const int gr = clamp_tile(floorf(tz + span), xl, xr);
+        if (gl <= gr) {
+            const float vl = row_lhs(r, gl), vr = row_lhs(r, gr);
+            const bool out_l = gl == xl || !(row_lhs(r, gl - 1) <= Kmax);
+            const bool out_r = gr == xr || !(row_lhs(r, gr + 1) <= Kmax);
+            if (vl <= Kmin && vr <= Kmin && out_l && out_r) {   // and I_min = I_max
+                a = gl;
+                b = gr;
+                return true;
+            }
+        }
+    }
     // vertex: the first tile t in [xl, xr + 1] at which l11 dxb + P has the
     // sign of l11 (xr + 1 counts as such); |.| is smallest at t or t - 1
     const float sg = l11 > 0.0f ? 1.0f : -1.0f;
-    const float tz = (mx - 8.0f - r.P / l11) * 0.0625f;
     int t = clamp_tile(floorf(tz) + 1.0f, xl, xr + 1);
     if (t <= xr && row_e1(r, t) * sg >= 0.0f) {
         int s = 0;
@@ -232,8 +252,7 @@ __device__ __forceinline__ bool row_tiles(float mx, float my, float l11, float l
         vm = fminf(v1, v0);
     }
     if (!(vm <= Kmax)) return true;   // the lowest point fails even the larger bound
-    // I_max from guesses at the real crossings |l11 dxb + P| = h1 + Kmax
-    const float span = (r.h1 + Kmax) / fabsf(l11) * 0.0625f;
+    // I_max from guesses at the real crossings
     float va, vb;
     const int a2 = row_first(r, Kmax, xl, tm, clamp_tile(floorf(tz - span) + 1.0f, xl, tm), va);
     const int b2 = row_last(r, Kmax, tm, xr, clamp_tile(floorf(tz + span), tm, xr), vb);
