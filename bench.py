@@ -500,6 +500,17 @@ def run_gpu(args):
         bins[name] = {"ms_per_frame": ms_, "algorithmic_bytes": b, "achieved_gbs": gbs,
                       "peak_gbs": peaks.get("hbm_gbs"),
                       "frac": gbs / peaks["hbm_gbs"] if gbs and peaks.get("hbm_gbs") else None}
+    # the scatter's list entries each go to a different tile's list: one
+    # 32-byte sector store per listed pair, against the measured rate of
+    # scattered sector stores
+    store_rate = m.mgs_probe_store(local)
+    n_pairs = sum(pairs) / len(pairs)
+    store_bound_ms = 1000.0 * n_pairs / (n_sm * store_rate * f_hz) if store_rate > 0 else None
+    bins["k_bin_scatter"].update({
+        "store_sectors": n_pairs,
+        "measured_sector_stores_per_sm_clk": store_rate,
+        "store_bound_ms": store_bound_ms,
+        "frac_store": store_bound_ms / per[4] if store_bound_ms and per[4] > 0 else None})
 
     if rank == 0:
         line = {

@@ -384,6 +384,17 @@ mgs_status mgs_render_static(const void *attrs, int64_t n, int32_t precision,
  * buffers.  MGS_ERR_INVALID_ARG for NULL outputs or a bad device. */
 mgs_status mgs_probe_rates(int32_t device, double *ex2_per_sm_clk, double *ffma_per_sm_clk);
 
+/* Measured rate of scattered 4-byte stores, one 32-byte sector each, per SM
+ * per clock cycle on CUDA device `device`: what bounds the list writes of
+ * tile binning (Sec. 2: lists keyed by tile only, each (tile, Gaussian) entry
+ * written to its tile's list, so consecutive entries of a warp land in
+ * different sectors).  Blocks of 256 threads write 256 words each to
+ * pseudo-random sector starts of a 64 MB device buffer (L2-resident, like the
+ * lists); per SM, sectors over the span of its blocks, averaged over the SMs.
+ * Synchronous; allocates and frees two device buffers.  MGS_ERR_INVALID_ARG
+ * for a NULL output or a bad device. */
+mgs_status mgs_probe_store(int32_t device, double *sectors_per_sm_clk);
+
 const char *mgs_last_error(void);
 const char *mgs_version(void);
 

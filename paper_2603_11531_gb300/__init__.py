@@ -46,7 +46,7 @@ EXPORTS = (
     "mgs_version", "mgs_workspace_set_timing", "mgs_workspace_stage_times",
     "mgs_render_static", "mgs_render_backward", "mgs_render_depth", "mgs_decode_sh",
     "mgs_server_create", "mgs_server_destroy", "mgs_server_submit", "mgs_server_wait",
-    "mgs_server_ticket", "mgs_server_stats", "mgs_now", "mgs_probe_rates", "mgs_frame_stats",
+    "mgs_server_ticket", "mgs_server_stats", "mgs_now", "mgs_probe_rates", "mgs_probe_store", "mgs_frame_stats",
 )
 MLP_GRAD_SIZE = 5957
 
@@ -129,6 +129,7 @@ def lib():
                                    ctypes.POINTER(mgs_sh_mlp), P, P], I32),
                 "mgs_probe_rates": ([I32, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)], I32),
+                "mgs_probe_store": ([I32, ctypes.POINTER(ctypes.c_double)], I32),
                 "mgs_last_error": ([], ctypes.c_char_p),
                 "mgs_version": ([], ctypes.c_char_p),
             }
@@ -499,6 +500,13 @@ def mgs_probe_rates(device: int = 0):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().mgs_probe_rates(int(device), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def mgs_probe_store(device: int = 0):
+    """Scattered 4-byte stores (one 32-byte sector each) per SM per clock, measured."""
+    a = ctypes.c_double()
+    _check(lib().mgs_probe_store(int(device), ctypes.byref(a)))
+    return a.value
 
 
 def mgs_version() -> str:
