@@ -286,14 +286,15 @@ __device__ __forceinline__ bool row_tiles(float mx, float my, float l11, float l
 // Plan cost of a rectangle row: kRowCost plus one unit per tile of the row.
 // The count resolves a row in about the same time whatever its width; the
 // scatter also writes the row's listed tiles (about 0.6 of its width).
-constexpr int kRowCost = 5;
+constexpr int kRowCost = 3;
 // Cost of a group in the work plan beyond its rows: a fixed charge for
 // visiting it (loading its 32 rectangles, the scans and the row split), so
 // that shares over sparse stretches of the scene (many Gaussians with one
-// or two rows each) stay short.  Measured on the 600k benchmark view: 512
-// balances the warps best among 32 ... 1024 (a visit costs about as much as
-// a hundred rows).
-constexpr int kGroupCost = 512;
+// or two rows each) stay short.  Measured on the 600k benchmark view with the
+// row certificate: a visit charge of 1024 with a row cost of 3 balanced the
+// warps best among 256 ... 1536 and 3 ... 8 (a visit costs about as much as a
+// hundred rows).
+constexpr int kGroupCost = 1024;
 
 // A lane's Gaussian of a group: rectangle and cull geometry, loaded together
 // (the geometry of a Gaussian without a rectangle is loaded but never used),

@@ -110,9 +110,17 @@ extern "C" mgs_status mgs_probe_store(int32_t device, double *sectors_per_sm_clk
         set_last_error("NULL argument");
         return MGS_ERR_INVALID_ARG;
     }
-    int prev = -1;
+    int prev = -1, ndev = 0;
+    // check the ordinal first: a failed cudaSetDevice would leave its error
+    // for the next launch of this thread to report
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_last_error("no such CUDA device");
+        return MGS_ERR_INVALID_ARG;
+    }
     cudaGetDevice(&prev);
     if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
         set_last_error("cannot select the device");
         return MGS_ERR_INVALID_ARG;
     }
@@ -151,9 +159,17 @@ extern "C" mgs_status mgs_probe_rates(int32_t device, double *ex2_per_sm_clk,
         set_last_error("NULL argument");
         return MGS_ERR_INVALID_ARG;
     }
-    int prev = -1;
+    int prev = -1, ndev = 0;
+    // check the ordinal first: a failed cudaSetDevice would leave its error
+    // for the next launch of this thread to report
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_last_error("no such CUDA device");
+        return MGS_ERR_INVALID_ARG;
+    }
     cudaGetDevice(&prev);
     if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
         set_last_error("cannot select the device");
         return MGS_ERR_INVALID_ARG;
     }

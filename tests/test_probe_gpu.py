@@ -30,5 +30,17 @@ def test_store_rate_is_plausible(m):
 
 
 def test_probes_reject_bad_arguments(m):
-    with pytest.raises(m.MGSError):
-        m.mgs_probe_store(1 << 20)
+    import torch
+    for probe in (m.mgs_probe_store, m.mgs_probe_rates):
+        with pytest.raises(m.MGSError) as e:
+            probe(1 << 20)
+        assert e.value.status == m.MGS_ERR_INVALID_ARG
+    # the refusal leaves no CUDA error behind for the next render to report
+    from paper_2603_11531_gb300 import synth
+    r = m.Renderer(0)
+    try:
+        h = r.load_scene(synth.uniform_scene(64, seed=3, precision="fp32"))
+        out = r.render(h, synth.look_at((0, 0, -3), (0, 0, 0), 64, 48, 60.0))
+        assert torch.isfinite(out["rgb"]).all()
+    finally:
+        r.close()
